@@ -1,0 +1,246 @@
+"""Load-incremented Newton-Raphson equilibrium solve (oracle side).
+
+Sec. 3.2 names two microscale solvers: an implicit updated-Lagrangian
+Newton method and dynamic relaxation (Algorithm 2).  Both target the same
+static state; the oracle takes the implicit route in plain double
+precision:
+
+  1. split F = R U (polar decomposition) and walk the load path
+     F_k = R_k U_k, k = 1..K (K = 4 by default, intermediate increments
+     converged to 1e-6 only), with R_k the rotation by k/K of R's angle
+     about its axis and U_k = I + (k/K)(U - I);
+  2. at each increment pin boundary nodes to x = F_k X (Eq. affine-bc) and
+     predict free nodes as F_k X + h, h the previous fluctuation
+     (Eq. micro_coords);
+  3. Newton on f_free(x) = 0 with K_ff + mu I factored by a sparse direct
+     solver (SuperLU, symmetric mode, diagonal pivots), mu raised until the
+     factor is positive definite so each step descends the stored energy,
+     and mu steered Levenberg-Marquardt style by the ratio of the actual to
+     the predicted energy decrease (the residual norm decides once energy
+     differences reach rounding);
+  4. stop at ||f_free||_2 <= max(tol * R_aff, 1e-16 sum EA) (R_aff from
+     ``network.reference_force_scale``); after the last increment check
+     that K_ff is positive semi-definite (an energy minimum, not a saddle)
+     and, if not, push along the most negative curvature direction and
+     re-solve, at most three times;
+  5. return sigma from the fiber virial and, as a self-check, from the
+     boundary reactions (the two forms of the average after Eq. hill-mandel).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg
+import scipy.sparse as sp
+import scipy.sparse.linalg as sla
+from scipy.spatial.transform import Rotation
+
+from .network import (boundary_virial_stress, convergence_threshold, fiber_virial_stress,
+                      internal_forces, prune, reference_force_scale, stiffness_free, total_energy)
+
+
+@dataclass
+class Solution:
+    sigma: np.ndarray              # (3,3) fiber-virial Cauchy stress
+    sigma_boundary: np.ndarray     # (3,3) boundary-reaction form (self-check)
+    x: np.ndarray                  # (N,3) positions; pruned nodes left at F X
+    residual: float                # ||f_free||_2 at return
+    R_ref: float
+    converged: bool
+    newton_iters: int
+    stable: bool | None            # K_ff positive semi-definite at x
+    saddle_escapes: int
+    kept: np.ndarray               # fiber mask after pruning
+    free: np.ndarray               # free-node mask after pruning
+    info: dict = field(default_factory=dict)
+
+
+def _factor(K, mu):
+    n = K.shape[0]
+    A = (K + mu * sp.identity(n, format="csc")).tocsc()
+    try:
+        lu = sla.splu(A, permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0,
+                      options=dict(SymmetricMode=True))
+    except RuntimeError:  # exactly singular: not positive definite
+        return None, False, -1
+    symmetric_pivots = np.array_equal(lu.perm_r, lu.perm_c)
+    neg = int((lu.U.diagonal() <= 0).sum())
+    return lu, symmetric_pivots and neg == 0, neg
+
+
+def _load_path(F, increments):
+    R, U = scipy.linalg.polar(F, side="right")
+    rv = Rotation.from_matrix(R).as_rotvec()
+    out = []
+    for k in range(1, increments + 1):
+        t = k / increments
+        Rk = Rotation.from_rotvec(t * rv).as_matrix()
+        Uk = np.eye(3) + t * (U - np.eye(3))
+        out.append(Rk @ Uk)
+    out[-1] = np.array(F, dtype=np.float64)  # the last increment is F itself
+    return out
+
+
+class _Problem:
+    def __init__(self, X, conn, L0, EA, B, free):
+        self.X, self.conn, self.L0, self.EA, self.B = X, conn, L0, EA, B
+        self.free_ids = np.nonzero(free)[0]
+        self.free_index = -np.ones(X.shape[0], np.int64)
+        self.free_index[self.free_ids] = np.arange(self.free_ids.size)
+
+    def place(self, x, xf):
+        y = x.copy()
+        y[self.free_ids] = xf.reshape(-1, 3)
+        return y
+
+    def residual(self, x):
+        return internal_forces(x, self.conn, self.L0, self.EA, self.B)[self.free_ids].ravel()
+
+    def energy(self, x):
+        return total_energy(x, self.conn, self.L0, self.EA, self.B)
+
+    def tangent(self, x):
+        return stiffness_free(x, self.conn, self.L0, self.EA, self.B, self.free_index, self.free_ids.size)
+
+
+def _newton(pb, x, tol_abs, max_iter):
+    """Energy-descending Newton on the free DOFs; returns (x, iters, ||r||, ok).
+
+    Levenberg-Marquardt trust region on the stored energy W: solve
+    (K + mu I) p = r with mu large enough for a positive definite factor,
+    accept when W decreases (gain ratio rho against the quadratic model),
+    divide mu by 10 after a good step (rho > 3/4), double it after a poor
+    one (rho < 1/4) or a rejected one.  Once the predicted decrease falls to the
+    rounding level of W, acceptance switches to a decrease of ||r||.
+    """
+    mu, nu = 0.0, 2.0
+    it = 0
+    r = pb.residual(x)
+    rn = float(np.linalg.norm(r))
+    W0 = pb.energy(x)
+    K = None
+    while rn > tol_abs and it < max_iter:
+        it += 1
+        if K is None:
+            K = pb.tangent(x)
+            dscale = max(float(np.abs(K.diagonal()).mean()), 1e-300)
+            mu_min = 1e-12 * dscale
+        for _ in range(80):
+            lu, pd, _neg = _factor(K, mu)
+            if pd:
+                break
+            mu = max(4.0 * mu, 1e-6 * dscale)
+        else:
+            return x, it, rn, False
+        p = lu.solve(r)
+        pred = float(r @ p) - 0.5 * float(p @ (K @ p))
+        xt = pb.place(x, x[pb.free_ids].ravel() + p)
+        Wt = pb.energy(xt)
+        rt = pb.residual(xt)
+        rtn = float(np.linalg.norm(rt))
+        if pred > 1e-12 * max(abs(W0), 1e-300):
+            rho = (W0 - Wt) / pred
+            accept = rho > 1e-4 and np.isfinite(rtn)
+        else:
+            rho = 1.0
+            accept = rtn < rn
+        if accept:
+            x, r, rn, W0 = xt, rt, rtn, Wt
+            K = None
+            if rho > 0.75:
+                mu *= 0.1
+            elif rho < 0.25:
+                mu *= 2.0
+            if mu < mu_min:
+                mu = 0.0
+            nu = 2.0
+        else:
+            mu = max(mu * nu, 1e-6 * dscale)
+            nu *= 2.0
+            if mu > 1e14 * dscale:
+                return x, it, rn, False
+    return x, it, rn, rn <= tol_abs
+
+
+def _lowest_mode(K):
+    n = K.shape[0]
+    if n <= 3000:
+        w, V = np.linalg.eigh(K.toarray())
+        return w[0], V[:, 0]
+    w, V = sla.eigsh(K, k=1, which="SA", tol=1e-8, maxiter=20 * n)
+    return w[0], V[:, 0]
+
+
+def solve(X, conn, L0, EA, B, is_boundary, F, V0=1.0, tol=1e-12, increments=4,
+          h0=None, max_newton=50000, check_stability=True, mid_tol=1e-6) -> Solution:
+    """Equilibrium and Cauchy stress of one RVE under deformation gradient F.
+
+    X (N,3), conn (E,2) RVE-local ids, L0/EA/B (E,), is_boundary (N,),
+    F (3,3) with det F > 0.  ``h0`` (N,3) warm-starts the fluctuation
+    h = x - F X; with a warm start the load is applied in one increment.
+    """
+    X = np.asarray(X, np.float64).reshape(-1, 3)
+    conn = np.asarray(conn).reshape(-1, 2).astype(np.int64)
+    L0 = np.asarray(L0, np.float64)
+    EA = np.broadcast_to(np.asarray(EA, np.float64), L0.shape).copy()
+    B = np.broadcast_to(np.asarray(B, np.float64), L0.shape).copy()
+    nb = np.asarray(is_boundary).astype(bool)
+    F = np.asarray(F, np.float64).reshape(3, 3)
+    detF = float(np.linalg.det(F))
+    if not detF > 0:
+        raise ValueError("det F must be positive")
+    kept, free = prune(conn, nb)
+    c, l0, ea, b = conn[kept], L0[kept], EA[kept], B[kept]
+    pb = _Problem(X, c, l0, ea, b, free)
+    R_ref = reference_force_scale(X, c, l0, ea, b, F)
+    volume = detF * V0
+
+    if h0 is None:
+        path = _load_path(F, increments)
+        h = np.zeros_like(X)
+    else:
+        path = [F]
+        h = np.asarray(h0, np.float64).reshape(-1, 3).copy()
+    total_it = 0
+    ok = True
+    x = X @ F.T
+    for k, Fk in enumerate(path):
+        last = k == len(path) - 1
+        x = X @ Fk.T
+        x[pb.free_ids] += h[pb.free_ids]
+        tol_k = tol if last else max(tol, mid_tol)
+        Rk = reference_force_scale(X, c, l0, ea, b, Fk)
+        if pb.free_ids.size:
+            x, it, rn, ok = _newton(pb, x, convergence_threshold(tol_k, Rk, ea), max_newton)
+            total_it += it
+        h = x - X @ Fk.T
+    escapes = 0
+    stable = None
+    if pb.free_ids.size and check_stability:
+        for escapes in range(4):
+            K = pb.tangent(x)
+            dscale = max(float(np.abs(K.diagonal()).mean()), 1e-300)
+            _, pd, _ = _factor(K, 1e-9 * dscale)
+            stable = bool(pd)
+            if stable or escapes == 3:
+                break
+            lam, vec = _lowest_mode(K)
+            step = 1e-3 * float(np.mean(l0)) * vec / max(np.abs(vec).max(), 1e-300)
+            x = pb.place(x, x[pb.free_ids].ravel() + step)
+            x, it, rn, ok = _newton(pb, x, convergence_threshold(tol, R_ref, ea), max_newton)
+            total_it += it
+    r = pb.residual(x) if pb.free_ids.size else np.zeros(0)
+    rn = float(np.linalg.norm(r))
+    sigma = fiber_virial_stress(x, c, l0, ea, b, volume)
+    sigma_b = boundary_virial_stress(x, c, l0, ea, b, nb, volume)
+    return Solution(sigma=sigma, sigma_boundary=sigma_b, x=x, residual=rn, R_ref=R_ref,
+                    converged=bool(rn <= convergence_threshold(tol, R_ref, ea)), newton_iters=total_it, stable=stable,
+                    saddle_escapes=escapes, kept=kept, free=free,
+                    info=dict(n_free=int(pb.free_ids.size), n_fibers=int(kept.sum())))
+
+
+def solve_network(net, F, **kw) -> Solution:
+    """``solve`` on an ``rvegen.Network``-like object (X, conn, L0, EA, B, is_boundary, V0)."""
+    return solve(net.X, net.conn, net.L0, net.EA, net.B, net.is_boundary, F, V0=net.V0, **kw)
