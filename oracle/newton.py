@@ -6,8 +6,8 @@ static state; the oracle takes the implicit route in plain double
 precision:
 
   1. split F = R U (polar decomposition) and walk the load path
-     F_k = R_k U_k, k = 1..K (K = 4 by default, intermediate increments
-     converged to 1e-6 only), with R_k the rotation by k/K of R's angle
+     F_k = R_k U_k, k = 1..K (intermediate increments converged to 1e-6
+     only), with R_k the rotation by k/K of R's angle
      about its axis and U_k = I + (k/K)(U - I);
   2. at each increment pin boundary nodes to x = F_k X (Eq. affine-bc) and
      predict free nodes as F_k X + h, h the previous fluctuation
@@ -25,6 +25,14 @@ precision:
      re-solve, at most three times;
   5. return sigma from the fiber virial and, as a self-check, from the
      boundary reactions (the two forms of the average after Eq. hill-mandel).
+
+The default is one increment (K = 1): the microscale solve of Algorithm 2
+starts from the affine state of the full F (h = 0, or a warm start), and a
+sub-isostatic network can hold several stable equilibria with different
+stresses; starting the energy descent from the same state as the method is
+the reading that makes the oracle's answer the method's answer.  K > 1
+follows the quasi-static load path instead (used in tests where the
+minimum is unique).
 """
 from __future__ import annotations
 
@@ -173,7 +181,7 @@ def _lowest_mode(K):
     return w[0], V[:, 0]
 
 
-def solve(X, conn, L0, EA, B, is_boundary, F, V0=1.0, tol=1e-12, increments=4,
+def solve(X, conn, L0, EA, B, is_boundary, F, V0=1.0, tol=1e-12, increments=1,
           h0=None, max_newton=50000, check_stability=True, mid_tol=1e-6) -> Solution:
     """Equilibrium and Cauchy stress of one RVE under deformation gradient F.
 
