@@ -1,0 +1,213 @@
+/*
+ * rve.h -- C ABI of the batched fiber-network RVE solver (GB300, sm_103a).
+ *
+ * The library solves the microscale problem of an FE^2 analysis of fibrous
+ * materials (arXiv 2306.09427): many independent representative volume
+ * elements (RVEs), each a 3-D truss network whose boundary nodes follow the
+ * macroscale deformation gradient F (affine boundary condition, Sec. 2,
+ * Eq. affine-bc).  Each RVE is relaxed to static force equilibrium by
+ * damped dynamic relaxation (Algorithm 2, Sec. 3.2) and homogenized to the
+ * volume-averaged Cauchy stress
+ *     sigma = (1/v) sum_e N_e (d_e (x) d_e) / |d_e|,   v = det(F) V0,
+ * the fiber form of the average that follows Eq. hill-mandel.  The calls
+ * are "batched" in the paper's sense (Sec. 4): they take a set of
+ * deformation gradients and return the stresses (and tangents) of the whole
+ * set at once.
+ *
+ * Fiber law: eps_G = (l^2/L0^2 - 1)/2, N = (EA/B)(exp(B eps_G) - 1), and
+ * N = EA eps_G when B = 0.  Force of fiber e = (i, j) on node i is
+ * N (x_j - x_i)/l.
+ *
+ * Conventions
+ *  - Every function returns RVE_OK (0) or a negative RVE_E* code; the
+ *    message of the last failure on the calling thread is rve_last_error().
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory on the batch's device (e.g. torch tensors' data_ptr()).
+ *  - F is row-major: F[9k + 3i + j] = F_ij of item k.  sigma likewise
+ *    (all 9 entries, symmetric).  dsigma/dF is [item][ij][kl]: 81 doubles
+ *    per item, entry 9(3i+j) + (3k+l).
+ *  - Device-pointer calls are asynchronous on `stream` (a cudaStream_t,
+ *    NULL = legacy default stream); outputs are valid once the stream
+ *    reaches that point.  The batch object is not thread safe: serialise
+ *    calls on one batch.
+ */
+#ifndef RVE_H
+#define RVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define RVE_OK 0
+#define RVE_EINVAL (-1)  /* bad argument or malformed network            */
+#define RVE_ENOMEM (-2)  /* device or host allocation failed             */
+#define RVE_ECUDA (-3)   /* a CUDA runtime call failed                   */
+#define RVE_EADMIT (-4)  /* request exceeds a configured capacity        */
+
+/* per-item status written by the solve calls */
+#define RVE_STATUS_CONVERGED 0 /* ||f_free||_2 <= max(tol R_aff, 1e-16 sum EA)      */
+#define RVE_STATUS_MAX_ITER 1  /* iteration cap hit; sigma is of the last iterate  */
+#define RVE_STATUS_NONFINITE 2 /* residual became NaN/Inf; sigma is not meaningful */
+#define RVE_STATUS_EMPTY 3     /* no free node left after pruning; sigma is exact
+                                  (boundary-to-boundary fibers only), 0 iterations  */
+
+/* precision / execution path */
+#define RVE_PREC_PLAIN_F64 0   /* one RVE at a time, several FP64 kernels per DR
+                                  iteration, convergence tested on the host
+                                  (the paper's naive approach, Sec. 4.3)         */
+#define RVE_PREC_MIXED 1       /* batched fused kernel: FP32 forces and updates,
+                                  FP64 residual norm and stress accumulation     */
+#define RVE_PREC_BATCHED_F64 2 /* batched fused kernel, FP64 throughout         */
+
+typedef struct rve_batch rve_batch; /* opaque, library owned */
+
+/*
+ * Solver options (Algorithm 2's tolerance, iteration cap and damping).
+ *  tol          relative residual: converged when ||f_free||_2 <=
+ *               max(tol * R_aff, 1e-16 * sum_e EA_e), R_aff the 2-norm of
+ *               the fiber forces at the affine state x = F X.  Default 1e-6.
+ *  max_iter     DR iteration cap (Algorithm 2's n_max).  Default 200000.
+ *  check_every  residual test and damping update interval k (>= 1).
+ *               Default 50.
+ *  precision    RVE_PREC_*; default RVE_PREC_MIXED.
+ *  warm_start   1: start each solve from the RVE's fluctuation h = x - F X
+ *               left by its previous solve in the same precision (0 after
+ *               create or rve_reset_state); 0: start from h = 0.  Default 0.
+ *  damping      > 0: constant mass-proportional damping c (the paper's
+ *               choice, Sec. 3.2); <= 0: c re-estimated every check_every
+ *               iterations from a Rayleigh quotient.  Default 0.
+ *  threads      threads per CTA for the batched kernels (0 = automatic).
+ */
+typedef struct rve_options {
+  double tol;
+  int32_t max_iter;
+  int32_t check_every;
+  int32_t precision;
+  int32_t warm_start;
+  double damping;
+  int32_t threads;
+  int32_t reserved[7];
+} rve_options;
+
+/* Fill *opt with the defaults above.  Never fails. */
+void rve_options_default(rve_options* opt);
+
+/*
+ * Create a batch of n_rve networks (Algorithm 2 set-up: connectivity,
+ * lumped mass data and upload to the device, done once per RVE; the
+ * packed per-RVE offset layout is the paper's PackedView, Sec. 4.3).
+ * All array arguments are HOST pointers and are copied; the caller keeps
+ * ownership.
+ *   device       CUDA device ordinal the batch lives on.
+ *   node_off     n_rve+1 int64, node range of RVE r is [node_off[r], node_off[r+1]).
+ *   X            3*N_total doubles, reference coordinates (row per node).
+ *   fiber_off    n_rve+1 int64, fiber range of RVE r.
+ *   conn         2*E_total int32, RVE-local node ids (0-based) of each fiber.
+ *   L0, EA, B    E_total doubles each: rest length (> 0), axial stiffness
+ *                (> 0), exponential nonlinearity (>= 0).
+ *   is_boundary  N_total bytes, nonzero for nodes pinned to x = F X.
+ *   V0           n_rve doubles, reference volume per RVE; NULL means the
+ *                volume of each RVE's bounding box.
+ *   opt          NULL for defaults.
+ * Validation (RVE_EINVAL): offsets start at 0 and do not decrease, node
+ * ids in range, no fiber joining a node to itself, finite coordinates,
+ * the parameter ranges above, at least one boundary node in an RVE that
+ * has fibers, at most 65534 free nodes and 32767 active fibers per RVE.
+ * Pruning: free nodes with no fiber path to the boundary and free nodes
+ * of degree <= 1 (repeatedly) are removed; their fibers carry no force at
+ * equilibrium, so sigma is unchanged.
+ * On success *out receives the batch; on failure *out is NULL.
+ */
+int rve_batch_create(rve_batch** out, int device, int64_t n_rve, const int64_t* node_off,
+                     const double* X, const int64_t* fiber_off, const int32_t* conn,
+                     const double* L0, const double* EA, const double* B,
+                     const uint8_t* is_boundary, const double* V0, const rve_options* opt);
+
+/* Replace the batch's options (validated as in create). */
+int rve_set_options(rve_batch* b, const rve_options* opt);
+
+/*
+ * Solve every RVE of the batch (Algorithm 2 to convergence, then the
+ * stress average after Eq. hill-mandel).
+ *   F       device, 9*n_rve doubles, det F > 0 expected (det F <= 0 gives
+ *           status RVE_STATUS_NONFINITE for that RVE).
+ *   tol     <= 0 keeps the batch option; max_iter <= 0 likewise.
+ *   sigma   device, 9*n_rve doubles (written).
+ *   iters   device, n_rve int32 DR iterations performed (may be NULL).
+ *   status  device, n_rve int32 RVE_STATUS_* (may be NULL).
+ */
+int rve_solve(rve_batch* b, const double* F, double tol, int32_t max_iter, double* sigma,
+              int32_t* iters, int32_t* status, void* stream);
+
+/*
+ * Solve the m RVEs listed in ids (HOST array of distinct RVE indices) with
+ * deformation gradients F[9k..] for ids[k]; outputs are indexed by k
+ * (device arrays of m items).  Used by the serving loop.
+ */
+int rve_solve_subset(rve_batch* b, const int64_t* ids, int64_t m, const double* F, double tol,
+                     int32_t max_iter, double* sigma, int32_t* iters, int32_t* status,
+                     void* stream);
+
+/*
+ * End-to-end variant of rve_solve with HOST buffers: copies F to the
+ * device, solves, copies sigma/iters/status back and synchronises.
+ * iters/status may be NULL.
+ */
+int rve_solve_host(rve_batch* b, const double* F, double tol, int32_t max_iter, double* sigma,
+                   int32_t* iters, int32_t* status);
+
+/*
+ * Stress and stress tangent: sigma(F) and the central-difference
+ * derivative dsigma_ij/dF_kl = (sigma_ij(F + h E_kl) - sigma_ij(F - h E_kl)) / 2h,
+ * E_kl = e_k (x) e_l, nine directions, i.e. 18 perturbed solves per RVE
+ * batched in one launch and warm-started from the base solution (the
+ * paper obtains its material stiffness from finite-difference microscale
+ * solves, Sec. 3.2).  h <= 0 means 1e-4.
+ *   F          device 9*n_rve; sigma device 9*n_rve; dsigma_dF device 81*n_rve;
+ *   status     device n_rve (worst status over the 19 solves) or NULL.
+ */
+int rve_tangent(rve_batch* b, const double* F, double h, double tol, int32_t max_iter,
+                double* sigma, double* dsigma_dF, int32_t* status, void* stream);
+
+/* Forget the warm-start state of the m RVEs in ids (HOST array); ids ==
+ * NULL resets every RVE.  Synchronous. */
+int rve_reset_state(rve_batch* b, const int64_t* ids, int64_t m);
+
+/* Sizes after pruning, for throughput accounting. */
+typedef struct rve_batch_info {
+  int64_t n_rve;
+  int64_t free_nodes;     /* sum over RVEs of free nodes kept            */
+  int64_t active_fibers;  /* fibers with >= 1 free end (updated per DR iteration) */
+  int64_t fixed_fibers;   /* boundary-to-boundary fibers (stress only)  */
+  int64_t pruned_fibers;  /* fibers removed by pruning                  */
+  int64_t n_bins;         /* size bins of the batched path               */
+  int64_t device_bytes;   /* device memory held by the batch             */
+} rve_batch_info;
+int rve_batch_get_info(const rve_batch* b, rve_batch_info* info);
+
+/* Per-RVE sizes after pruning (HOST arrays of n_rve, any may be NULL). */
+int rve_batch_get_sizes(const rve_batch* b, int32_t* free_nodes, int32_t* active_fibers,
+                        int32_t* fixed_fibers);
+
+/*
+ * Current node positions of RVE r in its reference node order (HOST
+ * array of 3 * n_nodes(r) doubles): x = F X + h for free nodes kept,
+ * x = F X for boundary and pruned nodes, using F (HOST, 9 doubles) and
+ * the fluctuation h left by the last solve in `precision`.  Synchronous.
+ */
+int rve_get_positions(rve_batch* b, int64_t r, const double* F, int32_t precision,
+                      double* x_out);
+
+/* Free everything the batch holds (NULL is ignored). */
+void rve_batch_destroy(rve_batch* b);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* rve_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RVE_H */

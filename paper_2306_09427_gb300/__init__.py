@@ -1,0 +1,15 @@
+"""Batched fiber-network RVE solver for GB300 (sm_103a).
+
+Python binding of the C ABI declared in ``include/rve.h``: argument
+marshalling only, every step of the solve runs in the CUDA kernels of
+``librve.so``.  Importing this package fails loudly when the library has
+not been built: there is no CPU fallback.
+"""
+from ._lib import (RVE_EADMIT, RVE_ECUDA, RVE_EINVAL, RVE_ENOMEM, RVE_OK, RVE_PREC_BATCHED_F64,
+                   RVE_PREC_MIXED, RVE_PREC_PLAIN_F64, RVE_STATUS_CONVERGED, RVE_STATUS_EMPTY,
+                   RVE_STATUS_MAX_ITER, RVE_STATUS_NONFINITE, RveBatch, RveError, lib, lib_path,
+                   rve_batch_create, rve_batch_destroy, rve_batch_get_info, rve_batch_get_sizes,
+                   rve_get_positions, rve_last_error, rve_options_default, rve_reset_state,
+                   rve_set_options, rve_solve, rve_solve_host, rve_solve_subset, rve_tangent)
+
+__all__ = [n for n in dir() if n.startswith(("rve_", "RVE_", "Rve"))] + ["lib", "lib_path"]

@@ -1,0 +1,203 @@
+"""ctypes binding of librve.so (names and arguments as in include/rve.h)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+lib_path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "librve.so")
+if not os.path.exists(lib_path):
+    raise ImportError(f"{lib_path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+                      "(the solver has no CPU fallback)")
+lib = C.CDLL(lib_path)
+
+RVE_OK, RVE_EINVAL, RVE_ENOMEM, RVE_ECUDA, RVE_EADMIT = 0, -1, -2, -3, -4
+RVE_STATUS_CONVERGED, RVE_STATUS_MAX_ITER, RVE_STATUS_NONFINITE, RVE_STATUS_EMPTY = 0, 1, 2, 3
+RVE_PREC_PLAIN_F64, RVE_PREC_MIXED, RVE_PREC_BATCHED_F64 = 0, 1, 2
+
+
+class rve_options(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("check_every", C.c_int32),
+                ("precision", C.c_int32), ("warm_start", C.c_int32), ("damping", C.c_double),
+                ("threads", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class rve_batch_info(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("n_rve", "free_nodes", "active_fibers", "fixed_fibers",
+                                         "pruned_fibers", "n_bins", "device_bytes")]
+
+
+_P = C.c_void_p
+_I64 = C.c_int64
+_I32 = C.c_int32
+_D = C.c_double
+
+
+def _sig(name, res, args):
+    f = getattr(lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+rve_options_default = _sig("rve_options_default", None, [C.POINTER(rve_options)])
+rve_batch_create = _sig("rve_batch_create", C.c_int, [C.POINTER(_P), C.c_int, _I64, _P, _P, _P, _P, _P, _P, _P, _P,
+                                                      _P, C.POINTER(rve_options)])
+rve_set_options = _sig("rve_set_options", C.c_int, [_P, C.POINTER(rve_options)])
+rve_solve = _sig("rve_solve", C.c_int, [_P, _P, _D, _I32, _P, _P, _P, _P])
+rve_solve_subset = _sig("rve_solve_subset", C.c_int, [_P, _P, _I64, _P, _D, _I32, _P, _P, _P, _P])
+rve_solve_host = _sig("rve_solve_host", C.c_int, [_P, _P, _D, _I32, _P, _P, _P])
+rve_tangent = _sig("rve_tangent", C.c_int, [_P, _P, _D, _D, _I32, _P, _P, _P, _P])
+rve_reset_state = _sig("rve_reset_state", C.c_int, [_P, _P, _I64])
+rve_batch_get_info = _sig("rve_batch_get_info", C.c_int, [_P, C.POINTER(rve_batch_info)])
+rve_batch_get_sizes = _sig("rve_batch_get_sizes", C.c_int, [_P, _P, _P, _P])
+rve_get_positions = _sig("rve_get_positions", C.c_int, [_P, _I64, _P, _I32, _P])
+rve_batch_destroy = _sig("rve_batch_destroy", None, [_P])
+rve_last_error = _sig("rve_last_error", C.c_char_p, [])
+
+
+class RveError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where} failed ({code}): {rve_last_error().decode()}")
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != RVE_OK:
+        raise RveError(rc, where)
+
+
+def _ptr(a) -> int | None:
+    """Address of a numpy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+        return a.ctypes.data
+    assert a.is_contiguous(), "tensors must be contiguous"
+    return a.data_ptr()
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def options(**kw) -> rve_options:
+    o = rve_options()
+    rve_options_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class RveBatch:
+    """Owner of an ``rve_batch`` handle; methods map one to one on the C calls."""
+
+    def __init__(self, packed, device: int = 0, **opts):
+        p = packed
+        self._keep = [np.ascontiguousarray(p.node_off, np.int64), np.ascontiguousarray(p.X, np.float64),
+                      np.ascontiguousarray(p.fiber_off, np.int64), np.ascontiguousarray(p.conn, np.int32),
+                      np.ascontiguousarray(p.L0, np.float64), np.ascontiguousarray(p.EA, np.float64),
+                      np.ascontiguousarray(p.B, np.float64), np.ascontiguousarray(p.is_boundary, np.uint8),
+                      None if p.V0 is None else np.ascontiguousarray(p.V0, np.float64)]
+        self.n_rve = int(self._keep[0].shape[0] - 1)
+        self.device = device
+        self.opt = options(**opts)
+        h = _P()
+        rc = rve_batch_create(C.byref(h), device, self.n_rve, *[_ptr(a) for a in self._keep], C.byref(self.opt))
+        _check(rc, "rve_batch_create")
+        self.h = h
+        self._keep = None
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            rve_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, **kw) -> None:
+        for k, v in kw.items():
+            setattr(self.opt, k, v)
+        _check(rve_set_options(self.h, C.byref(self.opt)), "rve_set_options")
+
+    def info(self) -> dict:
+        i = rve_batch_info()
+        _check(rve_batch_get_info(self.h, C.byref(i)), "rve_batch_get_info")
+        return {n: getattr(i, n) for n, _ in rve_batch_info._fields_}
+
+    def sizes(self):
+        nf, na, nb = (np.zeros(self.n_rve, np.int32) for _ in range(3))
+        _check(rve_batch_get_sizes(self.h, _ptr(nf), _ptr(na), _ptr(nb)), "rve_batch_get_sizes")
+        return nf, na, nb
+
+    def solve(self, F, tol: float = 0.0, max_iter: int = 0, sigma=None, iters=None, status=None, stream=None):
+        """F: CUDA float64 tensor (n, 9) or (n, 3, 3).  Returns (sigma, iters, status) tensors."""
+        import torch
+        n = self.n_rve
+        if sigma is None:
+            sigma = torch.empty((n, 9), dtype=torch.float64, device=F.device)
+        if iters is None:
+            iters = torch.empty(n, dtype=torch.int32, device=F.device)
+        if status is None:
+            status = torch.empty(n, dtype=torch.int32, device=F.device)
+        _check(rve_solve(self.h, _ptr(F), tol, max_iter, _ptr(sigma), _ptr(iters), _ptr(status),
+                         _stream_handle(stream)), "rve_solve")
+        return sigma, iters, status
+
+    def solve_subset(self, ids, F, tol: float = 0.0, max_iter: int = 0, sigma=None, iters=None, status=None,
+                     stream=None):
+        import torch
+        ids = np.ascontiguousarray(ids, np.int64)
+        m = ids.shape[0]
+        if sigma is None:
+            sigma = torch.empty((m, 9), dtype=torch.float64, device=F.device)
+        if iters is None:
+            iters = torch.empty(m, dtype=torch.int32, device=F.device)
+        if status is None:
+            status = torch.empty(m, dtype=torch.int32, device=F.device)
+        _check(rve_solve_subset(self.h, _ptr(ids), m, _ptr(F), tol, max_iter, _ptr(sigma), _ptr(iters),
+                                _ptr(status), _stream_handle(stream)), "rve_solve_subset")
+        return sigma, iters, status
+
+    def solve_host(self, F, tol: float = 0.0, max_iter: int = 0):
+        """F: numpy float64 (n, 9) or (n, 3, 3).  Returns numpy (sigma, iters, status)."""
+        F = np.ascontiguousarray(F, np.float64).reshape(self.n_rve, 9)
+        sigma = np.empty((self.n_rve, 9))
+        iters = np.empty(self.n_rve, np.int32)
+        status = np.empty(self.n_rve, np.int32)
+        _check(rve_solve_host(self.h, _ptr(F), tol, max_iter, _ptr(sigma), _ptr(iters), _ptr(status)),
+               "rve_solve_host")
+        return sigma, iters, status
+
+    def tangent(self, F, h: float = 1e-4, tol: float = 0.0, max_iter: int = 0, stream=None):
+        import torch
+        n = self.n_rve
+        sigma = torch.empty((n, 9), dtype=torch.float64, device=F.device)
+        D = torch.empty((n, 81), dtype=torch.float64, device=F.device)
+        status = torch.empty(n, dtype=torch.int32, device=F.device)
+        _check(rve_tangent(self.h, _ptr(F), h, tol, max_iter, _ptr(sigma), _ptr(D), _ptr(status),
+                           _stream_handle(stream)), "rve_tangent")
+        return sigma, D, status
+
+    def reset_state(self, ids=None) -> None:
+        if ids is None:
+            _check(rve_reset_state(self.h, None, 0), "rve_reset_state")
+        else:
+            ids = np.ascontiguousarray(ids, np.int64)
+            _check(rve_reset_state(self.h, _ptr(ids), ids.shape[0]), "rve_reset_state")
+
+    def positions(self, r: int, F, n_nodes: int, precision: int | None = None):
+        F = np.ascontiguousarray(F, np.float64).reshape(9)
+        x = np.empty((n_nodes, 3))
+        prec = self.opt.precision if precision is None else precision
+        _check(rve_get_positions(self.h, r, _ptr(F), prec, _ptr(x)), "rve_get_positions")
+        return x

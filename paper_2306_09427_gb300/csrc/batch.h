@@ -1,0 +1,106 @@
+// The library-owned batch object behind the opaque rve_batch handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "rve_internal.h"
+
+namespace rvegpu {
+
+#define RVE_CUDA_TRY(call)                                                              \
+  do {                                                                                  \
+    cudaError_t err__ = (call);                                                         \
+    if (err__ != cudaSuccess)                                                           \
+      return ::rvegpu::fail(RVE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(err__)); \
+  } while (0)
+
+// One launch configuration of the fused kernel and the work it runs.
+struct Bin {
+  int mode = 0;   // 0 resident, 1 streamed (SCR in shared), 2 streamed (SCR global)
+  int nt = 256;   // threads per CTA
+  int npt = 1;    // free nodes per thread
+  int per_sm = 1; // CTAs per SM the footprint allows (bin key)
+  size_t smem = 0;
+  std::vector<Work> work;
+  Work* d_work = nullptr;
+  int n = 0;
+};
+
+// Launch configuration chosen for one RVE.
+struct BinKey {
+  int mode, nt, npt, per_sm;
+  size_t smem;
+  bool operator==(const BinKey& o) const {
+    return mode == o.mode && nt == o.nt && npt == o.npt && per_sm == o.per_sm;
+  }
+};
+
+// Batched-path state of one arithmetic type (float: mixed, double: FP64).
+struct PathState {
+  bool ready = false;
+  std::vector<BinKey> key_of;   // per RVE
+  std::vector<Bin> bins;        // all-RVE solve
+  std::vector<Bin> tan_bins;    // tangent: 18 perturbed solves per RVE
+  void* d_state = nullptr;      // 4 T per free node (fluctuation h)
+  uint8_t* d_valid = nullptr;   // per RVE: state holds a previous solve
+  void* d_gP0 = nullptr;        // streamed-bin scratch (4 T per active fiber)
+  void* d_gP1 = nullptr;
+  void* d_gSCR = nullptr;
+  void* d_tan_state = nullptr;  // 18 x 4 T per free node
+  void* d_tan_g[3] = {};        // streamed-bin scratch of the tangent directions
+  std::vector<int> bin_of;      // per RVE: index into bins
+  std::vector<Work> work_of;    // per RVE: its work item in the all-RVE solve
+  Work* d_sub_work = nullptr;   // subset solves
+  size_t sub_cap = 0;
+};
+
+constexpr int N_SIDE_STREAMS = 6;
+constexpr int N_DIRS = 18;  // 9 directions x (+h, -h)
+
+}  // namespace rvegpu
+
+struct rve_batch {
+  int device = 0;
+  int64_t n_rve = 0;
+  rve_options opt{};
+  rvegpu::HostTopology topo;
+  int64_t total_nf = 0, total_na = 0, total_nb = 0;
+  // device topology
+  rvegpu::RveMeta* d_meta = nullptr;
+  rvegpu::FibD* d_fa = nullptr;
+  uint32_t* d_fij = nullptr;
+  rvegpu::FibD* d_fb = nullptr;
+  uint16_t* d_csr = nullptr;
+  uint32_t* d_ncsr = nullptr;
+  float* d_ncap = nullptr;
+  rvegpu::PathState pf, pd;
+  // plain FP64 path scratch (sized for the largest RVE)
+  double* d_pl = nullptr;
+  size_t pl_bytes = 0;
+  double* h_pl = nullptr;  // pinned, reduction read-back
+  // streams for concurrent bins
+  cudaStream_t side[rvegpu::N_SIDE_STREAMS] = {};
+  cudaStream_t hstream = nullptr;  // host-buffer solves
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[rvegpu::N_SIDE_STREAMS] = {};
+  // tangent scratch
+  double* d_tanF = nullptr;
+  double* d_tanS = nullptr;
+  int32_t* d_tanI = nullptr;
+  int32_t* d_tanSt = nullptr;
+  // host-API staging
+  double* d_hF = nullptr;
+  double* d_hS = nullptr;
+  int32_t* d_hI = nullptr;
+  int32_t* d_hSt = nullptr;
+  double* h_pin = nullptr;
+  size_t h_pin_bytes = 0;
+  rvegpu::Work* h_work_pin = nullptr;  // staging for subset work lists
+  size_t h_work_cap = 0;
+  cudaEvent_t ev_work = nullptr;       // last upload from h_work_pin done
+  size_t device_bytes = 0;
+  std::vector<void*> allocations;
+};

@@ -1,0 +1,705 @@
+// C ABI of the batched RVE solver (declared in include/rve.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "batch.h"
+#include "dr_fused.cuh"
+
+namespace rvegpu {
+
+namespace {
+thread_local std::string g_error;
+}
+
+void set_error(const std::string& msg) { g_error = msg; }
+int fail(int code, const std::string& msg) {
+  g_error = msg;
+  return code;
+}
+
+int launch_bin(const DrArgs<float>& a, const Bin& bin, cudaStream_t s);
+int launch_bin(const DrArgs<double>& a, const Bin& bin, cudaStream_t s);
+int plain_scratch_bytes(int nf_max, int na_max);
+int plain_solve_one(rve_batch* b, int r, int out, const double* F, double tol, int max_iter, double* sigma,
+                    int32_t* iters, int32_t* status, cudaStream_t s);
+
+namespace {
+
+#define TRY(x)                  \
+  do {                          \
+    const int rc__ = (x);       \
+    if (rc__ != RVE_OK) return rc__; \
+  } while (0)
+
+int dalloc(rve_batch* b, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    (void)cudaGetLastError();
+    return fail(RVE_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  b->allocations.push_back(*p);
+  b->device_bytes += bytes;
+  return RVE_OK;
+}
+
+template <class T>
+int upload(rve_batch* b, T** d, const std::vector<T>& h) {
+  TRY(dalloc(b, reinterpret_cast<void**>(d), h.size() * sizeof(T)));
+  if (!h.empty()) RVE_CUDA_TRY(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return RVE_OK;
+}
+
+int valid_options(const rve_options& o) {
+  if (!(o.tol > 0.0) || !std::isfinite(o.tol)) return fail(RVE_EINVAL, "tol must be > 0");
+  if (o.max_iter < 0) return fail(RVE_EINVAL, "max_iter must be >= 0");
+  if (o.check_every < 1) return fail(RVE_EINVAL, "check_every must be >= 1");
+  if (o.precision < RVE_PREC_PLAIN_F64 || o.precision > RVE_PREC_BATCHED_F64)
+    return fail(RVE_EINVAL, "unknown precision");
+  if (o.warm_start != 0 && o.warm_start != 1) return fail(RVE_EINVAL, "warm_start must be 0 or 1");
+  if (!std::isfinite(o.damping)) return fail(RVE_EINVAL, "damping must be finite");
+  if (o.threads != 0 && o.threads != 64 && o.threads != 128 && o.threads != 256 && o.threads != 512 &&
+      o.threads != 1024)
+    return fail(RVE_EINVAL, "threads must be 0, 64, 128, 256, 512 or 1024");
+  return RVE_OK;
+}
+
+// Launch configuration of one RVE in the fused kernel.
+template <typename T>
+int choose_key(int nf, int na, int threads, BinKey& k) {
+  if (nf > 4 * MAX_THREADS) return fail(RVE_EINVAL, "the batched path holds at most 4096 free nodes per RVE");
+  int nt;
+  if (threads > 0) {
+    nt = threads;
+  } else {
+    const int target = std::max(na / 5, (nf + 3) / 4);
+    nt = 64;
+    while (nt < target && nt < 1024) nt *= 2;
+  }
+  while (nf > 4 * nt && nt < 1024) nt *= 2;
+  auto npt_of = [](int nf_, int nt_) {
+    const int q = (nf_ + nt_ - 1) / nt_;
+    return q <= 1 ? 1 : (q <= 2 ? 2 : 4);
+  };
+  int npt = npt_of(nf, nt);
+  const size_t budget = SMEM_LIMIT - 1024;
+  size_t sm = smem_resident<T>(nf, na, nt);
+  int mode = 0;
+  if (sm > budget) {
+    nt = 1024;
+    npt = std::max(2, npt_of(nf, nt));
+    const size_t s1 = smem_streamed<T>(nf, na, nt, true);
+    if (s1 <= budget) {
+      mode = 1;
+      sm = s1;
+    } else {
+      mode = 2;
+      sm = smem_streamed<T>(nf, na, nt, false);
+      if (sm > budget) return fail(RVE_EINVAL, "RVE too large for the batched path");
+    }
+  }
+  const int by_smem = int((228 * 1024) / (sm + 1024 + 512));
+  const int by_thr = 2048 / nt;
+  k = BinKey{mode, nt, npt, std::max(1, std::min(by_smem, by_thr)), sm};
+  return RVE_OK;
+}
+
+template <typename T>
+PathState& path(rve_batch* b);
+template <>
+PathState& path<float>(rve_batch* b) {
+  return b->pf;
+}
+template <>
+PathState& path<double>(rve_batch* b) {
+  return b->pd;
+}
+
+int upload_bins(rve_batch* b, std::vector<Bin>& bins) {
+  for (Bin& bin : bins) {
+    bin.n = int(bin.work.size());
+    TRY(upload(b, &bin.d_work, bin.work));
+  }
+  return RVE_OK;
+}
+
+template <typename T>
+int ensure_path(rve_batch* b) {
+  PathState& P = path<T>(b);
+  if (P.ready) return RVE_OK;
+  const int64_t n = b->n_rve;
+  P.key_of.resize(n);
+  std::vector<BinKey> keys;
+  std::vector<std::vector<int>> members;
+  for (int64_t r = 0; r < n; ++r) {
+    const RveMeta& M = b->topo.meta[r];
+    BinKey k;
+    TRY(choose_key<T>(M.nf, M.na, b->opt.threads, k));
+    P.key_of[r] = k;
+    size_t j = 0;
+    while (j < keys.size() && !(keys[j] == k)) ++j;
+    if (j == keys.size()) {
+      keys.push_back(k);
+      members.emplace_back();
+    }
+    keys[j].smem = std::max(keys[j].smem, k.smem);
+    members[j].push_back(int(r));
+  }
+  // streamed-bin scratch offsets (main solves and tangent directions)
+  int64_t scr_main = 0, scr_tan = 0;
+  std::vector<int32_t> scr_of(n, 0), scr_tan_of(n, 0);
+  for (int64_t r = 0; r < n; ++r) {
+    if (P.key_of[r].mode == 0) continue;
+    scr_of[r] = int32_t(scr_main);
+    scr_main += b->topo.meta[r].na;
+    scr_tan_of[r] = int32_t(scr_tan);
+    scr_tan += int64_t(N_DIRS) * b->topo.meta[r].na;
+  }
+  if (scr_tan > INT32_MAX) return fail(RVE_EINVAL, "streamed scratch exceeds 32-bit offsets");
+  P.bins.clear();
+  P.tan_bins.clear();
+  for (size_t j = 0; j < keys.size(); ++j) {
+    std::vector<int>& mem = members[j];
+    std::stable_sort(mem.begin(), mem.end(),
+                     [&](int x, int y) { return b->topo.meta[x].na > b->topo.meta[y].na; });
+    Bin bin;
+    bin.mode = keys[j].mode;
+    bin.nt = keys[j].nt;
+    bin.npt = keys[j].npt;
+    bin.per_sm = keys[j].per_sm;
+    bin.smem = keys[j].smem;
+    Bin tb = bin;
+    for (int r : mem) bin.work.push_back(Work{r, r, b->topo.meta[r].node_off, 0, scr_of[r], 0});
+    for (int r : mem)
+      for (int d = 0; d < N_DIRS; ++d)
+        tb.work.push_back(Work{r, int32_t(d * n + r), int32_t(d * b->total_nf + b->topo.meta[r].node_off), 1,
+                               int32_t(scr_tan_of[r] + d * b->topo.meta[r].na), 0});
+    P.bins.push_back(std::move(bin));
+    P.tan_bins.push_back(std::move(tb));
+  }
+  // largest total work first so the long bins start early
+  auto work_of = [&](const Bin& x) {
+    int64_t w = 0;
+    for (const Work& wk : x.work) w += b->topo.meta[wk.rve].na;
+    return w;
+  };
+  std::stable_sort(P.bins.begin(), P.bins.end(), [&](const Bin& x, const Bin& y) { return work_of(x) > work_of(y); });
+  std::stable_sort(P.tan_bins.begin(), P.tan_bins.end(),
+                   [&](const Bin& x, const Bin& y) { return work_of(x) > work_of(y); });
+  P.bin_of.assign(size_t(n), -1);
+  P.work_of.assign(size_t(n), Work{});
+  for (size_t j = 0; j < P.bins.size(); ++j)
+    for (const Work& w : P.bins[j].work) {
+      P.bin_of[w.rve] = int(j);
+      P.work_of[w.rve] = w;
+    }
+  TRY(upload_bins(b, P.bins));
+  TRY(upload_bins(b, P.tan_bins));
+  TRY(dalloc(b, &P.d_state, sizeof(T) * 4 * size_t(std::max<int64_t>(b->total_nf, 1))));
+  RVE_CUDA_TRY(cudaMemset(P.d_state, 0, sizeof(T) * 4 * size_t(std::max<int64_t>(b->total_nf, 1))));
+  TRY(dalloc(b, reinterpret_cast<void**>(&P.d_valid), size_t(std::max<int64_t>(n, 1))));
+  RVE_CUDA_TRY(cudaMemset(P.d_valid, 0, size_t(std::max<int64_t>(n, 1))));
+  if (scr_main > 0) {
+    TRY(dalloc(b, &P.d_gP0, sizeof(T) * 4 * size_t(scr_main)));
+    TRY(dalloc(b, &P.d_gP1, sizeof(T) * 4 * size_t(scr_main)));
+    TRY(dalloc(b, &P.d_gSCR, sizeof(T) * 4 * size_t(scr_main)));
+  }
+  P.ready = true;
+  return RVE_OK;
+}
+
+// Run a list of bins on `s`, concurrently on side streams when there are several.
+template <typename T>
+int run_bins(rve_batch* b, const std::vector<Bin>& bins, const DrArgs<T>& a, cudaStream_t s) {
+  std::vector<const Bin*> live;
+  for (const Bin& x : bins)
+    if (x.n > 0) live.push_back(&x);
+  if (live.empty()) return RVE_OK;
+  if (live.size() == 1) return launch_bin(a, *live[0], s);
+  RVE_CUDA_TRY(cudaEventRecord(b->ev_fork, s));
+  const int ns = std::min<int>(N_SIDE_STREAMS, int(live.size()));
+  for (int k = 0; k < ns; ++k) RVE_CUDA_TRY(cudaStreamWaitEvent(b->side[k], b->ev_fork, 0));
+  for (size_t i = 0; i < live.size(); ++i) TRY(launch_bin(a, *live[i], b->side[i % ns]));
+  for (int k = 0; k < ns; ++k) {
+    RVE_CUDA_TRY(cudaEventRecord(b->ev_join[k], b->side[k]));
+    RVE_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_join[k], 0));
+  }
+  return RVE_OK;
+}
+
+template <typename T>
+DrArgs<T> make_args(rve_batch* b, const double* F, double tol, int max_iter, double* sigma, int32_t* iters,
+                    int32_t* status, void* state, int warm_start) {
+  PathState& P = path<T>(b);
+  DrArgs<T> a;
+  a.meta = b->d_meta;
+  a.fa = b->d_fa;
+  a.fij = b->d_fij;
+  a.fb = b->d_fb;
+  a.csr = b->d_csr;
+  a.ncsr = b->d_ncsr;
+  a.ncap = b->d_ncap;
+  a.work = nullptr;
+  a.n_work = 0;
+  a.F = F;
+  a.sigma = sigma;
+  a.iters = iters;
+  a.status = status;
+  a.state = static_cast<T*>(state);
+  a.valid = P.d_valid;
+  a.warm_start = warm_start;
+  a.gP0 = static_cast<T*>(P.d_gP0);
+  a.gP1 = static_cast<T*>(P.d_gP1);
+  a.gSCR = static_cast<T*>(P.d_gSCR);
+  a.tol = tol;
+  a.max_iter = max_iter;
+  a.check_every = b->opt.check_every;
+  a.damping = b->opt.damping;
+  return a;
+}
+
+int set_device(rve_batch* b) {
+  RVE_CUDA_TRY(cudaSetDevice(b->device));
+  return RVE_OK;
+}
+
+int solve_all(rve_batch* b, const double* F, double tol, int max_iter, double* sigma, int32_t* iters,
+              int32_t* status, cudaStream_t s) {
+  const int prec = b->opt.precision;
+  if (prec == RVE_PREC_MIXED) {
+    TRY(ensure_path<float>(b));
+    const DrArgs<float> a = make_args<float>(b, F, tol, max_iter, sigma, iters, status, b->pf.d_state, b->opt.warm_start);
+    return run_bins(b, b->pf.bins, a, s);
+  }
+  if (prec == RVE_PREC_BATCHED_F64) {
+    TRY(ensure_path<double>(b));
+    const DrArgs<double> a = make_args<double>(b, F, tol, max_iter, sigma, iters, status, b->pd.d_state, b->opt.warm_start);
+    return run_bins(b, b->pd.bins, a, s);
+  }
+  TRY(ensure_path<double>(b));  // state buffer shared with the FP64 batched path
+  for (int64_t r = 0; r < b->n_rve; ++r)
+    TRY(plain_solve_one(b, int(r), int(r), F, tol, max_iter, sigma, iters, status, s));
+  return RVE_OK;
+}
+
+template <typename T>
+__global__ void tan_copy_state(const T* __restrict__ st, T* __restrict__ tan, int64_t total_nf) {
+  const int64_t n4 = 4 * total_nf;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < int64_t(N_DIRS) * n4;
+       i += int64_t(gridDim.x) * blockDim.x)
+    tan[i] = st[i % n4];
+}
+
+__global__ void tan_make_F(const double* __restrict__ F, double* __restrict__ Fp, int64_t n, double h) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < int64_t(N_DIRS) * n;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t d = i / n, r = i % n;
+    const int dir = int(d / 2);
+    const double sgn = (d % 2 == 0) ? 1.0 : -1.0;
+    for (int k = 0; k < 9; ++k) Fp[9 * i + k] = F[9 * r + k] + (k == dir ? sgn * h : 0.0);
+  }
+}
+
+__global__ void tan_finish(const double* __restrict__ S, const int32_t* __restrict__ St, int64_t n, double h,
+                           double* __restrict__ D, int32_t* __restrict__ status) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < 81 * n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / 81;
+    const int ij = int(i % 81) / 9, kl = int(i % 81) % 9;
+    const double sp = S[9 * ((2 * kl) * n + r) + ij];
+    const double sm = S[9 * ((2 * kl + 1) * n + r) + ij];
+    D[i] = (sp - sm) / (2.0 * h);
+    if (status && i % 81 == 0) {
+      int w = status[r];
+      for (int d = 0; d < N_DIRS; ++d) w = max(w, St[d * n + r] == RVE_STATUS_EMPTY ? 0 : St[d * n + r]);
+      status[r] = w;
+    }
+  }
+}
+
+template <typename T>
+int tangent_batched(rve_batch* b, const double* F, double h, double tol, int max_iter, double* sigma,
+                    double* dsdF, int32_t* status, cudaStream_t s) {
+  TRY(ensure_path<T>(b));
+  PathState& P = path<T>(b);
+  const int64_t n = b->n_rve;
+  if (!b->d_tanF) {
+    TRY(dalloc(b, reinterpret_cast<void**>(&b->d_tanF), sizeof(double) * 9 * N_DIRS * size_t(n)));
+    TRY(dalloc(b, reinterpret_cast<void**>(&b->d_tanS), sizeof(double) * 9 * N_DIRS * size_t(n)));
+    TRY(dalloc(b, reinterpret_cast<void**>(&b->d_tanI), sizeof(int32_t) * (N_DIRS + 1) * size_t(n)));
+    TRY(dalloc(b, reinterpret_cast<void**>(&b->d_tanSt), sizeof(int32_t) * (N_DIRS + 1) * size_t(n)));
+  }
+  if (!P.d_tan_state) TRY(dalloc(b, &P.d_tan_state, sizeof(T) * 4 * N_DIRS * size_t(std::max<int64_t>(b->total_nf, 1))));
+  int32_t* st_base = status ? status : b->d_tanSt + N_DIRS * n;
+  int32_t* it_base = b->d_tanI + N_DIRS * n;
+  // base solve
+  const DrArgs<T> a0 = make_args<T>(b, F, tol, max_iter, sigma, it_base, st_base, P.d_state, b->opt.warm_start);
+  TRY(run_bins(b, P.bins, a0, s));
+  // perturbed solves, warm-started from the base fluctuation
+  if (b->total_nf > 0) {
+    tan_copy_state<T><<<1024, 256, 0, s>>>(static_cast<const T*>(P.d_state), static_cast<T*>(P.d_tan_state), b->total_nf);
+    RVE_CUDA_TRY(cudaGetLastError());
+  }
+  if (n > 0) {
+    tan_make_F<<<256, 256, 0, s>>>(F, b->d_tanF, n, h);
+    RVE_CUDA_TRY(cudaGetLastError());
+  }
+  DrArgs<T> a1 = make_args<T>(b, b->d_tanF, tol, max_iter, b->d_tanS, b->d_tanI, b->d_tanSt, P.d_tan_state, 1);
+  // the tangent bins have their own streamed scratch (18 directions per RVE)
+  int64_t scr = 0;
+  for (const Bin& bin : P.tan_bins)
+    if (bin.mode != 0)
+      for (const Work& w : bin.work) scr += b->topo.meta[w.rve].na;
+  if (scr > 0) {
+    if (!P.d_tan_g[0])
+      for (int k = 0; k < 3; ++k) TRY(dalloc(b, &P.d_tan_g[k], sizeof(T) * 4 * size_t(scr)));
+    a1.gP0 = static_cast<T*>(P.d_tan_g[0]);
+    a1.gP1 = static_cast<T*>(P.d_tan_g[1]);
+    a1.gSCR = static_cast<T*>(P.d_tan_g[2]);
+  }
+  TRY(run_bins(b, P.tan_bins, a1, s));
+  if (n > 0) {
+    tan_finish<<<512, 256, 0, s>>>(b->d_tanS, b->d_tanSt, n, h, dsdF, status);
+    RVE_CUDA_TRY(cudaGetLastError());
+  }
+  return RVE_OK;
+}
+
+}  // namespace
+}  // namespace rvegpu
+
+using namespace rvegpu;
+
+extern "C" {
+
+void rve_options_default(rve_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-6;
+  o->max_iter = 200000;
+  o->check_every = 50;
+  o->precision = RVE_PREC_MIXED;
+  o->warm_start = 0;
+  o->damping = 0.0;
+  o->threads = 0;
+}
+
+const char* rve_last_error(void) { return g_error.c_str(); }
+
+int rve_set_options(rve_batch* b, const rve_options* opt) {
+  if (!b || !opt) return fail(RVE_EINVAL, "null argument");
+  TRY(valid_options(*opt));
+  const bool retune = opt->threads != b->opt.threads;
+  b->opt = *opt;
+  if (retune) {
+    b->pf.ready = false;  // bins depend on the thread count; rebuilt lazily
+    b->pd.ready = false;
+  }
+  return RVE_OK;
+}
+
+int rve_batch_create(rve_batch** out, int device, int64_t n_rve, const int64_t* node_off, const double* X,
+                     const int64_t* fiber_off, const int32_t* conn, const double* L0, const double* EA,
+                     const double* B, const uint8_t* is_boundary, const double* V0, const rve_options* opt) {
+  if (!out) return fail(RVE_EINVAL, "out is null");
+  *out = nullptr;
+  rve_options o;
+  rve_options_default(&o);
+  if (opt) o = *opt;
+  TRY(valid_options(o));
+  // host-side validation and layout first: malformed input fails without touching a GPU
+  rve_batch* b = new rve_batch();
+  b->n_rve = n_rve;
+  b->opt = o;
+  int rc = build_topology(n_rve, node_off, X, fiber_off, conn, L0, EA, B, is_boundary, V0, b->topo);
+  if (rc != RVE_OK) {
+    delete b;
+    return rc;
+  }
+  int ndev = 0;
+  const cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || device < 0 || device >= ndev) {
+    delete b;
+    (void)cudaGetLastError();
+    return fail(ce != cudaSuccess ? RVE_ECUDA : RVE_EINVAL,
+                ce != cudaSuccess ? std::string("no usable CUDA device: ") + cudaGetErrorString(ce)
+                                  : std::string("device ordinal out of range"));
+  }
+  b->device = device;
+  auto bail = [&](int rc_) {
+    rve_batch_destroy(b);
+    return rc_;
+  };
+  for (const RveMeta& M : b->topo.meta) {
+    b->total_nf += M.nf;
+    b->total_na += M.na;
+    b->total_nb += M.nb;
+  }
+  if ((rc = set_device(b)) != RVE_OK) return bail(rc);
+  if ((rc = upload(b, &b->d_meta, b->topo.meta)) != RVE_OK) return bail(rc);
+  if ((rc = upload(b, &b->d_fa, b->topo.fa)) != RVE_OK) return bail(rc);
+  if ((rc = upload(b, &b->d_fij, b->topo.fij)) != RVE_OK) return bail(rc);
+  if ((rc = upload(b, &b->d_fb, b->topo.fb)) != RVE_OK) return bail(rc);
+  if ((rc = upload(b, &b->d_csr, b->topo.csr)) != RVE_OK) return bail(rc);
+  if ((rc = upload(b, &b->d_ncsr, b->topo.ncsr)) != RVE_OK) return bail(rc);
+  if ((rc = upload(b, &b->d_ncap, b->topo.ncap)) != RVE_OK) return bail(rc);
+  int nf_max = 0, na_max = 0;
+  for (const RveMeta& M : b->topo.meta) {
+    nf_max = std::max(nf_max, M.nf);
+    na_max = std::max(na_max, M.na);
+  }
+  b->pl_bytes = size_t(plain_scratch_bytes(nf_max, na_max)) + 16 * 256;
+  if ((rc = dalloc(b, reinterpret_cast<void**>(&b->d_pl), b->pl_bytes)) != RVE_OK) return bail(rc);
+  if (cudaMallocHost(reinterpret_cast<void**>(&b->h_pl), 64 * sizeof(double)) != cudaSuccess)
+    return bail(fail(RVE_ENOMEM, "cudaMallocHost failed"));
+  for (int k = 0; k < N_SIDE_STREAMS; ++k) {
+    if (cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) != cudaSuccess)
+      return bail(fail(RVE_ECUDA, "stream/event creation failed"));
+  }
+  if (cudaStreamCreateWithFlags(&b->hstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_work, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(RVE_ECUDA, "event creation failed"));
+  *out = b;
+  return RVE_OK;
+}
+
+int rve_solve(rve_batch* b, const double* F, double tol, int32_t max_iter, double* sigma, int32_t* iters,
+              int32_t* status, void* stream) {
+  if (!b) return fail(RVE_EINVAL, "null batch");
+  if (b->n_rve == 0) return RVE_OK;
+  if (!F || !sigma) return fail(RVE_EINVAL, "F and sigma are required");
+  TRY(set_device(b));
+  if (!(tol > 0.0)) tol = b->opt.tol;
+  if (max_iter <= 0) max_iter = b->opt.max_iter;
+  return solve_all(b, F, tol, max_iter, sigma, iters, status, static_cast<cudaStream_t>(stream));
+}
+
+int rve_solve_subset(rve_batch* b, const int64_t* ids, int64_t m, const double* F, double tol, int32_t max_iter,
+                     double* sigma, int32_t* iters, int32_t* status, void* stream) {
+  if (!b) return fail(RVE_EINVAL, "null batch");
+  if (m == 0) return RVE_OK;
+  if (m < 0 || !ids || !F || !sigma) return fail(RVE_EINVAL, "bad subset arguments");
+  if (m > INT32_MAX) return fail(RVE_EINVAL, "subset too large");
+  TRY(set_device(b));
+  if (!(tol > 0.0)) tol = b->opt.tol;
+  if (max_iter <= 0) max_iter = b->opt.max_iter;
+  std::vector<uint8_t> seen(size_t(b->n_rve), 0);
+  for (int64_t k = 0; k < m; ++k) {
+    if (ids[k] < 0 || ids[k] >= b->n_rve) return fail(RVE_EINVAL, "subset id out of range");
+    if (seen[ids[k]]++) return fail(RVE_EINVAL, "subset ids must be distinct");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int prec = b->opt.precision;
+  if (prec == RVE_PREC_PLAIN_F64) {
+    TRY(ensure_path<double>(b));
+    for (int64_t k = 0; k < m; ++k)
+      TRY(plain_solve_one(b, int(ids[k]), int(k), F, tol, max_iter, sigma, iters, status, s));
+    return RVE_OK;
+  }
+  const bool f32 = prec == RVE_PREC_MIXED;
+  if (f32) TRY(ensure_path<float>(b));
+  else TRY(ensure_path<double>(b));
+  PathState& P = f32 ? b->pf : b->pd;
+  // group ids by bin of the all-RVE solve
+  std::vector<Bin> bins(P.bins.size());
+  for (size_t j = 0; j < bins.size(); ++j) {
+    bins[j].mode = P.bins[j].mode;
+    bins[j].nt = P.bins[j].nt;
+    bins[j].npt = P.bins[j].npt;
+    bins[j].per_sm = P.bins[j].per_sm;
+    bins[j].smem = P.bins[j].smem;
+  }
+  for (int64_t k = 0; k < m; ++k) {
+    const int r = int(ids[k]);
+    Work w = P.work_of[r];
+    w.out = int32_t(k);
+    bins[P.bin_of[r]].work.push_back(w);
+  }
+  for (Bin& x : bins)
+    std::stable_sort(x.work.begin(), x.work.end(),
+                     [&](const Work& p, const Work& q) { return b->topo.meta[p.rve].na > b->topo.meta[q.rve].na; });
+  // stage work lists: wait for the previous upload from the pinned buffer
+  if (size_t(m) > b->h_work_cap) {
+    RVE_CUDA_TRY(cudaEventSynchronize(b->ev_work));
+    if (b->h_work_pin) cudaFreeHost(b->h_work_pin);
+    b->h_work_pin = nullptr;
+    const size_t cap = std::max<size_t>(size_t(m), 1024);
+    RVE_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&b->h_work_pin), cap * sizeof(Work)));
+    b->h_work_cap = cap;
+  }
+  if (size_t(m) > P.sub_cap) {
+    void* p = nullptr;
+    TRY(dalloc(b, &p, std::max<size_t>(size_t(m), 1024) * sizeof(Work)));
+    P.d_sub_work = static_cast<Work*>(p);
+    P.sub_cap = std::max<size_t>(size_t(m), 1024);
+  }
+  RVE_CUDA_TRY(cudaEventSynchronize(b->ev_work));
+  size_t off = 0;
+  for (Bin& x : bins) {
+    std::copy(x.work.begin(), x.work.end(), b->h_work_pin + off);
+    x.d_work = P.d_sub_work + off;
+    x.n = int(x.work.size());
+    off += x.work.size();
+  }
+  RVE_CUDA_TRY(cudaMemcpyAsync(P.d_sub_work, b->h_work_pin, off * sizeof(Work), cudaMemcpyHostToDevice, s));
+  RVE_CUDA_TRY(cudaEventRecord(b->ev_work, s));
+  if (f32) {
+    const DrArgs<float> a = make_args<float>(b, F, tol, max_iter, sigma, iters, status, b->pf.d_state, b->opt.warm_start);
+    return run_bins(b, bins, a, s);
+  }
+  const DrArgs<double> a = make_args<double>(b, F, tol, max_iter, sigma, iters, status, b->pd.d_state, b->opt.warm_start);
+  return run_bins(b, bins, a, s);
+}
+
+int rve_solve_host(rve_batch* b, const double* F, double tol, int32_t max_iter, double* sigma, int32_t* iters,
+                   int32_t* status) {
+  if (!b) return fail(RVE_EINVAL, "null batch");
+  if (b->n_rve == 0) return RVE_OK;
+  if (!F || !sigma) return fail(RVE_EINVAL, "F and sigma are required");
+  TRY(set_device(b));
+  const size_t n = size_t(b->n_rve);
+  if (!b->d_hF) {
+    TRY(dalloc(b, reinterpret_cast<void**>(&b->d_hF), 9 * n * sizeof(double)));
+    TRY(dalloc(b, reinterpret_cast<void**>(&b->d_hS), 9 * n * sizeof(double)));
+    TRY(dalloc(b, reinterpret_cast<void**>(&b->d_hI), n * sizeof(int32_t)));
+    TRY(dalloc(b, reinterpret_cast<void**>(&b->d_hSt), n * sizeof(int32_t)));
+    const size_t bytes = 9 * n * sizeof(double) * 2 + 2 * n * sizeof(int32_t);
+    RVE_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&b->h_pin), bytes));
+    b->h_pin_bytes = bytes;
+  }
+  double* pF = b->h_pin;
+  double* pS = b->h_pin + 9 * n;
+  int32_t* pI = reinterpret_cast<int32_t*>(b->h_pin + 18 * n);
+  int32_t* pSt = pI + n;
+  std::memcpy(pF, F, 9 * n * sizeof(double));
+  cudaStream_t s = b->hstream;
+  RVE_CUDA_TRY(cudaMemcpyAsync(b->d_hF, pF, 9 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+  TRY(rve_solve(b, b->d_hF, tol, max_iter, b->d_hS, b->d_hI, b->d_hSt, s));
+  RVE_CUDA_TRY(cudaMemcpyAsync(pS, b->d_hS, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  RVE_CUDA_TRY(cudaMemcpyAsync(pI, b->d_hI, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  RVE_CUDA_TRY(cudaMemcpyAsync(pSt, b->d_hSt, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  RVE_CUDA_TRY(cudaStreamSynchronize(s));
+  std::memcpy(sigma, pS, 9 * n * sizeof(double));
+  if (iters) std::memcpy(iters, pI, n * sizeof(int32_t));
+  if (status) std::memcpy(status, pSt, n * sizeof(int32_t));
+  return RVE_OK;
+}
+
+int rve_tangent(rve_batch* b, const double* F, double h, double tol, int32_t max_iter, double* sigma,
+                double* dsigma_dF, int32_t* status, void* stream) {
+  if (!b) return fail(RVE_EINVAL, "null batch");
+  if (b->n_rve == 0) return RVE_OK;
+  if (!F || !sigma || !dsigma_dF) return fail(RVE_EINVAL, "F, sigma and dsigma_dF are required");
+  TRY(set_device(b));
+  if (!(h > 0.0)) h = 1e-4;
+  if (!(tol > 0.0)) tol = b->opt.tol;
+  if (max_iter <= 0) max_iter = b->opt.max_iter;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (b->opt.precision == RVE_PREC_MIXED) return tangent_batched<float>(b, F, h, tol, max_iter, sigma, dsigma_dF, status, s);
+  if (b->opt.precision == RVE_PREC_BATCHED_F64)
+    return tangent_batched<double>(b, F, h, tol, max_iter, sigma, dsigma_dF, status, s);
+  return fail(RVE_EINVAL, "rve_tangent needs a batched precision (RVE_PREC_MIXED or RVE_PREC_BATCHED_F64)");
+}
+
+int rve_reset_state(rve_batch* b, const int64_t* ids, int64_t m) {
+  if (!b) return fail(RVE_EINVAL, "null batch");
+  TRY(set_device(b));
+  RVE_CUDA_TRY(cudaDeviceSynchronize());
+  for (PathState* P : {&b->pf, &b->pd}) {
+    if (!P->ready) continue;
+    if (!ids) {
+      RVE_CUDA_TRY(cudaMemset(P->d_valid, 0, size_t(std::max<int64_t>(b->n_rve, 1))));
+      continue;
+    }
+    for (int64_t k = 0; k < m; ++k) {
+      if (ids[k] < 0 || ids[k] >= b->n_rve) return fail(RVE_EINVAL, "reset id out of range");
+      RVE_CUDA_TRY(cudaMemset(P->d_valid + ids[k], 0, 1));
+    }
+  }
+  return RVE_OK;
+}
+
+int rve_batch_get_info(const rve_batch* b, rve_batch_info* info) {
+  if (!b || !info) return fail(RVE_EINVAL, "null argument");
+  info->n_rve = b->n_rve;
+  info->free_nodes = b->total_nf;
+  info->active_fibers = b->total_na;
+  info->fixed_fibers = b->total_nb;
+  info->pruned_fibers = b->topo.pruned_fibers;
+  info->n_bins = int64_t(std::max(b->pf.bins.size(), b->pd.bins.size()));
+  info->device_bytes = int64_t(b->device_bytes);
+  return RVE_OK;
+}
+
+int rve_batch_get_sizes(const rve_batch* b, int32_t* free_nodes, int32_t* active_fibers, int32_t* fixed_fibers) {
+  if (!b) return fail(RVE_EINVAL, "null batch");
+  for (int64_t r = 0; r < b->n_rve; ++r) {
+    const RveMeta& M = b->topo.meta[r];
+    if (free_nodes) free_nodes[r] = M.nf;
+    if (active_fibers) active_fibers[r] = M.na;
+    if (fixed_fibers) fixed_fibers[r] = M.nb;
+  }
+  return RVE_OK;
+}
+
+int rve_get_positions(rve_batch* b, int64_t r, const double* F, int32_t precision, double* x_out) {
+  if (!b || !F || !x_out) return fail(RVE_EINVAL, "null argument");
+  if (r < 0 || r >= b->n_rve) return fail(RVE_EINVAL, "RVE index out of range");
+  TRY(set_device(b));
+  const RveMeta& M = b->topo.meta[r];
+  const int64_t n0 = b->topo.node_off_in[r];
+  for (int i = 0; i < M.n_nodes; ++i)
+    for (int k = 0; k < 3; ++k) {
+      const double* X = &b->topo.X_in[3 * (n0 + i)];
+      x_out[3 * i + k] = F[3 * k] * X[0] + F[3 * k + 1] * X[1] + F[3 * k + 2] * X[2];
+    }
+  const bool f32 = precision == RVE_PREC_MIXED;
+  PathState& P = f32 ? b->pf : b->pd;
+  if (!P.ready || M.nf == 0) return RVE_OK;
+  RVE_CUDA_TRY(cudaDeviceSynchronize());
+  uint8_t valid = 0;
+  RVE_CUDA_TRY(cudaMemcpy(&valid, P.d_valid + r, 1, cudaMemcpyDeviceToHost));
+  if (!valid) return RVE_OK;
+  std::vector<double> h(4 * size_t(M.nf));
+  if (f32) {
+    std::vector<float> hf(4 * size_t(M.nf));
+    RVE_CUDA_TRY(cudaMemcpy(hf.data(), static_cast<float*>(P.d_state) + 4 * size_t(M.node_off),
+                            hf.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < hf.size(); ++i) h[i] = hf[i];
+  } else {
+    RVE_CUDA_TRY(cudaMemcpy(h.data(), static_cast<double*>(P.d_state) + 4 * size_t(M.node_off),
+                            h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  for (int a = 0; a < M.nf; ++a) {
+    const int i = b->topo.free_node_id[M.node_off + a];
+    for (int k = 0; k < 3; ++k) x_out[3 * i + k] += h[4 * a + k];
+  }
+  return RVE_OK;
+}
+
+void rve_batch_destroy(rve_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  for (void* p : b->allocations) cudaFree(p);
+  for (int k = 0; k < N_SIDE_STREAMS; ++k) {
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+  }
+  if (b->hstream) cudaStreamDestroy(b->hstream);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_work) cudaEventDestroy(b->ev_work);
+  if (b->h_pl) cudaFreeHost(b->h_pl);
+  if (b->h_pin) cudaFreeHost(b->h_pin);
+  if (b->h_work_pin) cudaFreeHost(b->h_work_pin);
+  delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,6 @@
+// Fused batched kernel, mixed precision (FP32 forces/updates, FP64 sums).
+#include "dr_launch.cuh"
+
+namespace rvegpu {
+int launch_bin(const DrArgs<float>& a, const Bin& bin, cudaStream_t s) { return launch_bin_t<float>(a, bin, s); }
+}  // namespace rvegpu

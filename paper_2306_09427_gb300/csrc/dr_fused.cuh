@@ -1,0 +1,531 @@
+// Fused batched dynamic-relaxation kernel: one CTA solves one RVE.
+//
+// Per work item (RVE r, deformation gradient F):
+//   set-up   per active fiber e = (i, j): the affine chord g_e = F dX_e and
+//            the affine Green strain a_e = (dX.E.dX + (|dX|^2 - L0^2)/2)/L0^2,
+//            E = (F^T F - I)/2, both in FP64; boundary-to-boundary fibers
+//            have a fixed length, so their stress share and the affine force
+//            norm R_aff are summed here once, in FP64.
+//   loop     (Algorithm 2, Sec. 3.2)
+//     fiber  with the fluctuation difference u = h_j - h_i (boundary ends
+//            read the zero slot, h = 0 under the affine BC, Eq. affine-bc):
+//              eps = a_e + u.(2 g_e + u) / (2 L0^2)      (no cancellation)
+//              d = g_e + u,  l = |d|,  N = (EA/B) expm1(B eps)
+//              s = N / l,  sbar = max(dN/dl, |N|/l)
+//            and stores (s d, sbar) in the fiber scratch SCR;
+//     gather each free node sums +-(s d) and sbar of its incident fibers in
+//            a fixed CSR order (deterministic, no atomics; the paper's
+//            getInternalForces scatters with atomics, Sec. 4.3);
+//     check  every check_every iterations: ||f_free||_2 in FP64 against
+//            max(tol R_aff, 1e-16 sum EA); damping re-estimated;
+//     update m = MASS_COEF sbar_sum, v <- ((2-c) v + 2 f/m)/(2+c),
+//            |v| capped, h <- h + v (dt = 1).
+//   finish   sigma = (sigma_bb + sum_e s_e d_e (x) d_e) / (det F V0) with
+//            FP64 compensated (TwoSum) accumulation; h saved for warm starts.
+//
+// Threads own fixed free nodes (a = tid + q*NT, q < NPT) whose h, v, cap
+// and CSR range live in registers; the shared array H publishes h to the
+// fiber phase.  MODE 0 keeps all per-fiber data of the RVE in shared
+// memory; MODE 1 reads fiber parameters and CSR from global memory (L2)
+// and keeps H and SCR in shared memory; MODE 2 also moves SCR to global.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rve_internal.h"
+
+namespace rvegpu {
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  using t = float4;
+};
+struct __align__(16) dvec4 {
+  double x, y, z, w;
+};
+template <>
+struct Vec4<double> {
+  using t = dvec4;
+};
+
+// Minimum resident CTAs per SM requested from the register allocator:
+// about 85 registers per thread for CTAs of up to 256 threads.
+template <int NT>
+constexpr int min_blocks() {
+  return NT >= 1024 ? 1 : (NT >= 512 ? 1 : (768 / NT));
+}
+
+__device__ __forceinline__ float k_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double k_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float k_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double k_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ uint32_t k_unpack_ij(float w) { return __float_as_uint(w); }
+__device__ __forceinline__ uint32_t k_unpack_ij(double w) { return static_cast<uint32_t>(w); }
+__device__ __forceinline__ float k_pack_ij(uint32_t ij, float) { return __uint_as_float(ij); }
+__device__ __forceinline__ double k_pack_ij(uint32_t ij, double) { return static_cast<double>(ij); }
+
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Neumaier accumulator
+struct CSum {
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double x) {
+    double t, e;
+    two_sum(s, x, t, e);
+    s = t;
+    c += e;
+  }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void warp_csum(double& s, double& c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const double c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    double t, e;
+    two_sum(s, s2, t, e);
+    s = t;
+    c = c + c2 + e;
+  }
+}
+
+// Sum K doubles over the block; every thread gets the totals.  One
+// barrier; the caller separates successive uses of `red` by a barrier.
+template <int NT, int K>
+__device__ __forceinline__ void block_allreduce(double (&v)[K], double* red) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[warp * K + k] = v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+#pragma unroll 4
+    for (int w = 0; w < NT / 32; ++w) s += red[w * K + k];
+    v[k] = s;
+  }
+}
+
+// Fiber force from the fluctuation formulation (see header comment).
+template <typename T, typename V4>
+__device__ __forceinline__ void fiber_force(const V4& p0, const V4& p1, const V4& hi, const V4& hj,
+                                            T& Dx, T& Dy, T& Dz, T& s, T& sbar) {
+  const T ux = hj.x - hi.x, uy = hj.y - hi.y, uz = hj.z - hi.z;
+  const T t = ux * (T(2) * p0.x + ux) + uy * (T(2) * p0.y + uy) + uz * (T(2) * p0.z + uz);
+  const T eps = t * p1.x + p0.w;
+  Dx = p0.x + ux;
+  Dy = p0.y + uy;
+  Dz = p0.z + uz;
+  const T l2 = Dx * Dx + Dy * Dy + Dz * Dz;
+  const T rl = k_rsqrt(l2);
+  const T l = l2 * rl;
+  T phi, ex, ea;
+  if (p1.z > T(0)) {
+    phi = k_expm1(p1.z * eps);
+    ex = phi + T(1);
+    ea = p1.y * p1.z;
+  } else {
+    phi = eps;
+    ex = T(1);
+    ea = p1.y;
+  }
+  const T N = p1.y * phi;
+  s = N * rl;
+  const T kax = ea * ex * l * (T(2) * p1.x);
+  sbar = fmax(kax, fabs(s));
+}
+
+// Fiber law in FP64 for set-up terms: N(eps) with the B = 0 limit.
+__device__ __forceinline__ double law_f64(double eps, double EA, double B) {
+  return B > 0.0 ? (EA / B) * expm1(B * eps) : EA * eps;
+}
+
+template <typename T, int NT, int NPT, int MODE>
+__global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const DrArgs<T> A) {
+  using V4 = typename Vec4<T>::t;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sF[9], sE[9];
+  __shared__ double sRes[8], sBB[12];
+
+  const Work wk = A.work[blockIdx.x];
+  const RveMeta M = A.meta[wk.rve];
+  const int tid = threadIdx.x;
+  const int nf = M.nf, na = M.na, nb = M.nb;
+
+  // ---- shared-memory carve-up
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    unsigned char* p = smem + off;
+    off += align_up(bytes, 16);
+    return p;
+  };
+  V4* H = reinterpret_cast<V4*>(carve(size_t(nf + 1) * sizeof(V4)));
+  V4* P0;
+  V4* P1;
+  V4* SCR;
+  const uint16_t* CSR;
+  if constexpr (MODE == 0) {
+    P0 = reinterpret_cast<V4*>(carve(size_t(na) * sizeof(V4)));
+    P1 = reinterpret_cast<V4*>(carve(size_t(na) * sizeof(V4)));
+    SCR = reinterpret_cast<V4*>(carve(size_t(na) * sizeof(V4)));
+    CSR = reinterpret_cast<const uint16_t*>(carve(size_t(2 * na) * sizeof(uint16_t)));
+  } else {
+    P0 = reinterpret_cast<V4*>(A.gP0) + wk.scr_off;
+    P1 = reinterpret_cast<V4*>(A.gP1) + wk.scr_off;
+    if constexpr (MODE == 1)
+      SCR = reinterpret_cast<V4*>(carve(size_t(na) * sizeof(V4)));
+    else
+      SCR = reinterpret_cast<V4*>(A.gSCR) + wk.scr_off;
+    CSR = A.csr + M.csr_off;
+  }
+  double* red = reinterpret_cast<double*>(carve(size_t(NT / 32) * 12 * sizeof(double) + 256));
+
+  if (tid < 9) sF[tid] = A.F[9 * size_t(wk.out) + tid];
+  __syncthreads();
+  if (tid < 9) {
+    const int k = tid / 3, l = tid % 3;
+    sE[tid] = 0.5 * (sF[k] * sF[l] + sF[3 + k] * sF[3 + l] + sF[6 + k] * sF[6 + l] - (k == l ? 1.0 : 0.0));
+  }
+  __syncthreads();
+  const double detF = sF[0] * (sF[4] * sF[8] - sF[5] * sF[7]) - sF[1] * (sF[3] * sF[8] - sF[5] * sF[6]) +
+                      sF[2] * (sF[3] * sF[7] - sF[4] * sF[6]);
+  const bool badF = !(detF > 0.0) || !(detF < 1e300);  // inverted, degenerate or non-finite F
+
+  // ---- set-up: affine terms of active fibers (FP64), loop parameters
+  double raff2 = 0.0;
+  for (int e = tid; e < na; e += NT) {
+    const FibD q = A.fa[M.fa_off + e];
+    const double gx = sF[0] * q.dx + sF[1] * q.dy + sF[2] * q.dz;
+    const double gy = sF[3] * q.dx + sF[4] * q.dy + sF[5] * q.dz;
+    const double gz = sF[6] * q.dx + sF[7] * q.dy + sF[8] * q.dz;
+    const double ex = sE[0] * q.dx + sE[1] * q.dy + sE[2] * q.dz;
+    const double ey = sE[3] * q.dx + sE[4] * q.dy + sE[5] * q.dz;
+    const double ez = sE[6] * q.dx + sE[7] * q.dy + sE[8] * q.dz;
+    const double L02 = q.L0 * q.L0;
+    const double a = (q.dx * ex + q.dy * ey + q.dz * ez + 0.5 * (q.dx * q.dx + q.dy * q.dy + q.dz * q.dz - L02)) / L02;
+    const double Na = law_f64(a, q.EA, q.B);
+    raff2 += Na * Na;
+    V4 p0, p1;
+    p0.x = T(gx);
+    p0.y = T(gy);
+    p0.z = T(gz);
+    p0.w = T(a);
+    p1.x = T(0.5 / L02);
+    p1.y = T(q.B > 0.0 ? q.EA / q.B : q.EA);
+    p1.z = T(q.B);
+    p1.w = k_pack_ij(A.fij[M.fa_off + e], T(0));
+    P0[e] = p0;
+    P1[e] = p1;
+  }
+  // boundary-to-boundary fibers: fixed length, stress share summed once
+  CSum sb6[6];
+  for (int e = tid; e < nb; e += NT) {
+    const FibD q = A.fb[M.fb_off + e];
+    const double gx = sF[0] * q.dx + sF[1] * q.dy + sF[2] * q.dz;
+    const double gy = sF[3] * q.dx + sF[4] * q.dy + sF[5] * q.dz;
+    const double gz = sF[6] * q.dx + sF[7] * q.dy + sF[8] * q.dz;
+    const double ex = sE[0] * q.dx + sE[1] * q.dy + sE[2] * q.dz;
+    const double ey = sE[3] * q.dx + sE[4] * q.dy + sE[5] * q.dz;
+    const double ez = sE[6] * q.dx + sE[7] * q.dy + sE[8] * q.dz;
+    const double L02 = q.L0 * q.L0;
+    const double a = (q.dx * ex + q.dy * ey + q.dz * ez + 0.5 * (q.dx * q.dx + q.dy * q.dy + q.dz * q.dz - L02)) / L02;
+    const double N = law_f64(a, q.EA, q.B);
+    raff2 += N * N;
+    const double s = N / sqrt(gx * gx + gy * gy + gz * gz);
+    sb6[0].add(s * gx * gx);
+    sb6[1].add(s * gy * gy);
+    sb6[2].add(s * gz * gz);
+    sb6[3].add(s * gy * gz);
+    sb6[4].add(s * gx * gz);
+    sb6[5].add(s * gx * gy);
+  }
+  if constexpr (MODE == 0) {
+    uint16_t* csr_s = const_cast<uint16_t*>(CSR);
+    const uint16_t* csr_g = A.csr + M.csr_off;
+    for (int k = tid; k < 2 * na; k += NT) csr_s[k] = csr_g[k];
+  }
+  // owned free nodes
+  const bool warm = wk.kind == 1 || (A.warm_start && A.valid[wk.rve]);
+  T hx[NPT], hy[NPT], hz[NPT], vx[NPT], vy[NPT], vz[NPT];
+  float cap[NPT];
+  uint32_t cs[NPT];
+#pragma unroll
+  for (int q = 0; q < NPT; ++q) {
+    const int a = tid + q * NT;
+    hx[q] = hy[q] = hz[q] = T(0);
+    vx[q] = vy[q] = vz[q] = T(0);
+    cap[q] = 0.f;
+    cs[q] = 0u;
+    if (a < nf) {
+      if (warm) {
+        const V4 s4 = reinterpret_cast<const V4*>(A.state)[size_t(wk.state_off) + a];
+        hx[q] = s4.x;
+        hy[q] = s4.y;
+        hz[q] = s4.z;
+      }
+      cap[q] = A.ncap[M.node_off + a];
+      cs[q] = A.ncsr[M.node_off + a];
+      V4 h4;
+      h4.x = hx[q];
+      h4.y = hy[q];
+      h4.z = hz[q];
+      h4.w = T(0);
+      H[a] = h4;
+    }
+  }
+  if (tid == 0) {
+    V4 z;
+    z.x = z.y = z.z = z.w = T(0);
+    H[nf] = z;
+  }
+  // boundary-fiber stress share (compensated) -> sBB, then R_aff
+  {
+    const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      double s = sb6[k].s, cc = sb6[k].c;
+      warp_csum(s, cc);
+      if (lane == 0) {
+        red[(warp * 6 + k) * 2 + 0] = s;
+        red[(warp * 6 + k) * 2 + 1] = cc;
+      }
+    }
+    __syncthreads();
+    if (tid < 6) {
+      double s = 0.0, cc = 0.0;
+      for (int w = 0; w < NT / 32; ++w) {
+        double t, e;
+        two_sum(s, red[(w * 6 + tid) * 2 + 0], t, e);
+        s = t;
+        cc += e + red[(w * 6 + tid) * 2 + 1];
+      }
+      sBB[2 * tid] = s;
+      sBB[2 * tid + 1] = cc;
+    }
+    __syncthreads();
+  }
+  {
+    double v1[1] = {raff2};
+    block_allreduce<NT, 1>(v1, red);
+    raff2 = v1[0];
+  }
+  const double thr = fmax(A.tol * sqrt(raff2), ABS_FLOOR * M.sum_EA);
+  const double thr2 = thr * thr;
+  __syncthreads();  // red reuse and set-up writes visible
+
+  // ---- dynamic relaxation loop
+  const int K = A.check_every;
+  const bool adaptive = !(A.damping > 0.0);
+  double c = adaptive ? DAMP_C0 : A.damping;
+  T alpha = T((2.0 - c) / (2.0 + c)), beta = T(2.0 / (2.0 + c));
+  double pre = 0.0, pm = 0.0;  // thread partials from the iteration before a check
+  bool have_pre = false;
+  int it = 0;
+  int status = RVE_STATUS_EMPTY;
+  if (nf > 0 && !badF) {
+    status = RVE_STATUS_MAX_ITER;
+    for (;; ++it) {
+      // fiber phase
+      for (int e = tid; e < na; e += NT) {
+        const V4 p0 = P0[e];
+        const V4 p1 = P1[e];
+        const uint32_t ij = k_unpack_ij(p1.w);
+        const V4 hi = H[ij & 0xffffu];
+        const V4 hj = H[ij >> 16];
+        T Dx, Dy, Dz, s, sbar;
+        fiber_force<T>(p0, p1, hi, hj, Dx, Dy, Dz, s, sbar);
+        V4 o;
+        o.x = s * Dx;
+        o.y = s * Dy;
+        o.z = s * Dz;
+        o.w = sbar;
+        SCR[e] = o;
+      }
+      __syncthreads();
+      // gather
+      T fx[NPT], fy[NPT], fz[NPT], fw[NPT];
+#pragma unroll
+      for (int q = 0; q < NPT; ++q) {
+        fx[q] = fy[q] = fz[q] = fw[q] = T(0);
+        const int a = tid + q * NT;
+        if (a < nf) {
+          const uint32_t b = cs[q] >> 8, n = cs[q] & 0xffu;
+          for (uint32_t k = 0; k < n; ++k) {
+            const uint32_t ent = CSR[b + k];
+            const V4 s4 = SCR[ent >> 1];
+            if (ent & 1u) {
+              fx[q] -= s4.x;
+              fy[q] -= s4.y;
+              fz[q] -= s4.z;
+            } else {
+              fx[q] += s4.x;
+              fy[q] += s4.y;
+              fz[q] += s4.z;
+            }
+            fw[q] += s4.w;
+          }
+        }
+      }
+      const bool check = (it % K == 0) || (it >= A.max_iter);
+      if (check) {
+        double v3[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+          if (tid + q * NT < nf) {
+            v3[0] += double(fx[q]) * double(fx[q]) + double(fy[q]) * double(fy[q]) + double(fz[q]) * double(fz[q]);
+            v3[1] += double(vx[q]) * double(fx[q]) + double(vy[q]) * double(fy[q]) + double(vz[q]) * double(fz[q]);
+          }
+        }
+        v3[1] -= pre;
+        v3[2] = pm;
+        block_allreduce<NT, 3>(v3, red);
+        if (!(v3[0] < 1e300)) {  // NaN or Inf
+          status = RVE_STATUS_NONFINITE;
+          break;
+        }
+        if (v3[0] <= thr2) {
+          status = RVE_STATUS_CONVERGED;
+          break;
+        }
+        if (it >= A.max_iter) break;
+        if (adaptive && have_pre && v3[2] > 0.0) {
+          const double lam = -v3[1] / v3[2];
+          if (lam > 0.0) {
+            c = fmin(2.0 * sqrt(lam), DAMP_C_MAX);
+            alpha = T((2.0 - c) / (2.0 + c));
+            beta = T(2.0 / (2.0 + c));
+          }
+        }
+        pre = 0.0;
+        pm = 0.0;
+        have_pre = false;
+      }
+      const bool pre_it = adaptive && ((it + 1) % K == 0);
+      // update owned nodes
+#pragma unroll
+      for (int q = 0; q < NPT; ++q) {
+        const int a = tid + q * NT;
+        if (a < nf) {
+          const T m = T(MASS_COEF) * fw[q];
+          const T bm = beta / m;
+          T nvx = alpha * vx[q] + bm * fx[q];
+          T nvy = alpha * vy[q] + bm * fy[q];
+          T nvz = alpha * vz[q] + bm * fz[q];
+          const T sp2 = nvx * nvx + nvy * nvy + nvz * nvz;
+          const T cp = T(cap[q]);
+          if (sp2 > cp * cp) {
+            const T sc = cp * k_rsqrt(sp2);
+            nvx *= sc;
+            nvy *= sc;
+            nvz *= sc;
+          }
+          vx[q] = nvx;
+          vy[q] = nvy;
+          vz[q] = nvz;
+          hx[q] += nvx;
+          hy[q] += nvy;
+          hz[q] += nvz;
+          V4 h4;
+          h4.x = hx[q];
+          h4.y = hy[q];
+          h4.z = hz[q];
+          h4.w = T(0);
+          H[a] = h4;
+          if (pre_it) {
+            pre += double(nvx) * double(fx[q]) + double(nvy) * double(fy[q]) + double(nvz) * double(fz[q]);
+            pm += double(m) * (double(nvx) * double(nvx) + double(nvy) * double(nvy) + double(nvz) * double(nvz));
+          }
+        }
+      }
+      if (pre_it) have_pre = true;
+      __syncthreads();
+    }
+  }
+
+  // ---- stress: active fibers at the final state (H holds it)
+  CSum s6[6];
+  for (int e = tid; e < na; e += NT) {
+    const V4 p0 = P0[e];
+    const V4 p1 = P1[e];
+    const uint32_t ij = k_unpack_ij(p1.w);
+    const V4 hi = H[ij & 0xffffu];
+    const V4 hj = H[ij >> 16];
+    T Dx, Dy, Dz, s, sbar;
+    fiber_force<T>(p0, p1, hi, hj, Dx, Dy, Dz, s, sbar);
+    const double sd = double(s), dx = double(Dx), dy = double(Dy), dz = double(Dz);
+    s6[0].add(sd * dx * dx);
+    s6[1].add(sd * dy * dy);
+    s6[2].add(sd * dz * dz);
+    s6[3].add(sd * dy * dz);
+    s6[4].add(sd * dx * dz);
+    s6[5].add(sd * dx * dy);
+  }
+  __syncthreads();  // red free (last allreduce read before the previous barrier)
+  const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double s = s6[k].s, cc = s6[k].c;
+    warp_csum(s, cc);
+    if (lane == 0) {
+      red[(warp * 6 + k) * 2 + 0] = s;
+      red[(warp * 6 + k) * 2 + 1] = cc;
+    }
+  }
+  __syncthreads();
+  if (tid < 6) {
+    double s = sBB[2 * tid], cc = sBB[2 * tid + 1];
+    for (int w = 0; w < NT / 32; ++w) {
+      double t, e;
+      two_sum(s, red[(w * 6 + tid) * 2 + 0], t, e);
+      s = t;
+      cc += e + red[(w * 6 + tid) * 2 + 1];
+    }
+    sRes[tid] = s + cc;
+  }
+  // save state
+#pragma unroll
+  for (int q = 0; q < NPT; ++q) {
+    const int a = tid + q * NT;
+    if (a < nf) {
+      V4 h4;
+      h4.x = hx[q];
+      h4.y = hy[q];
+      h4.z = hz[q];
+      h4.w = T(0);
+      reinterpret_cast<V4*>(A.state)[size_t(wk.state_off) + a] = h4;
+    }
+  }
+  __syncthreads();
+  if (tid < 9) {
+    // sigma components in order xx yy zz yz xz xy
+    const int i = tid / 3, j = tid % 3;
+    const int map[9] = {0, 5, 4, 5, 1, 3, 4, 3, 2};
+    A.sigma[9 * size_t(wk.out) + tid] = badF ? __longlong_as_double(0x7ff8000000000000ll)
+                                              : sRes[map[3 * i + j]] / (detF * M.V0);
+  }
+  if (tid == 0) {
+    int st = status;
+    if (badF) st = RVE_STATUS_NONFINITE;
+    if (wk.kind == 0) A.valid[wk.rve] = (st == RVE_STATUS_NONFINITE) ? 0 : 1;  // never warm-start from NaN
+    if (A.iters) A.iters[wk.out] = it;
+    if (A.status) A.status[wk.out] = st;
+  }
+}
+
+}  // namespace rvegpu

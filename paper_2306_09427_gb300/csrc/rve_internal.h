@@ -1,0 +1,155 @@
+// Internal data layout of an RVE batch (host and device).
+//
+// Storage is structure-of-arrays with per-RVE offsets: every RVE's free
+// nodes, active fibers (at least one free end), boundary-to-boundary
+// fibers and CSR entries sit in contiguous segments of batch-wide arrays
+// (the packed row-offset/value layout of the paper's PackedView, Sec. 4.3).
+// Free nodes are numbered 0..nf-1 inside an RVE; fixed (boundary) nodes
+// are not stored at all: under the affine boundary condition their
+// fluctuation h = x - F X is identically zero (Eq. affine-bc vs
+// Eq. micro_coords), so a fiber end on the boundary reads the zero slot nf.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace rvegpu {
+
+// Static per-fiber record, double precision (read once per solve).
+struct FibD {
+  double dx, dy, dz;  // X_j - X_i (reference chord)
+  double L0, EA, B;
+};
+
+// Per-RVE metadata, one per RVE on the device.
+struct RveMeta {
+  int32_t nf;       // free nodes kept
+  int32_t na;       // active fibers
+  int32_t nb;       // boundary-to-boundary fibers
+  int32_t n_nodes;  // nodes in the input (for position export)
+  int32_t node_off; // offset into per-free-node arrays
+  int32_t fa_off;   // offset into active-fiber arrays
+  int32_t fb_off;   // offset into boundary-fiber arrays
+  int32_t csr_off;  // offset into CSR entries (2*na per RVE)
+  double V0;        // reference volume
+  double sum_EA;    // sum of EA over kept fibers (absolute residual floor)
+};
+
+// One unit of work of a batched launch: solve RVE `rve` with F[9*out..],
+// write outputs at index `out`, keep the fluctuation state at
+// state_off (in free nodes) of the state buffer.
+struct Work {
+  int32_t rve;
+  int32_t out;
+  int32_t state_off;
+  int32_t kind;     // 0: the RVE's own state slot (warm start if enabled and
+                    //    valid, marks it valid); 1: scratch slot, always warm
+  int32_t scr_off;  // streamed bins: offset (in fibers) of this item's
+                    // global P0/P1/SCR scratch
+  int32_t pad;
+};
+
+// Dynamic-relaxation constants of the explicit update (Sec. 3.2: the
+// mass, damping and time step are fictitious and chosen for speed).
+//   lumped mass   m_i = MASS_GAMMA * (dt^2/4) * sum_e 2 max(k_e, |N_e|/l_e),
+//                 dt = 1, re-evaluated every iteration from the current state
+//                 (a Gershgorin bound on the stiffness, so the central
+//                 difference step stays stable as fibers stiffen);
+//   step cap      |x_i^{n+1} - x_i^n| <= STEP_CAP * min_{e at i} L0_e;
+//   damping       c0 at start, then c = 2 sqrt(lambda) (critical for the
+//                 lowest mode) from a Rayleigh quotient, c <= C_MAX.
+constexpr double MASS_GAMMA = 1.1;
+constexpr double MASS_COEF = MASS_GAMMA * 0.25 * 2.0;
+constexpr double STEP_CAP = 0.1;
+constexpr double DAMP_C0 = 0.1;
+constexpr double DAMP_C_MAX = 1.9;
+constexpr double ABS_FLOOR = 1e-16;  // absolute residual floor per unit EA
+
+// Shared-memory footprint of one RVE held by the fused kernel.
+// resident: P0, P1, SCR (one 4-vector each per active fiber), H (nf+1
+// 4-vectors), CSR entries (2*na u16) and a reduction buffer.
+// streamed: H and SCR only when they fit, otherwise H only.
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+inline size_t red_bytes(int nt) { return align_up(size_t(nt / 32) * 12 * sizeof(double) + 256, 16); }
+template <typename T>
+inline size_t smem_resident(int nf, int na, int nt) {
+  const size_t v4 = 4 * sizeof(T);
+  return 3 * align_up(size_t(na) * v4, 16) + align_up(size_t(nf + 1) * v4, 16) +
+         align_up(size_t(2 * na) * sizeof(uint16_t), 16) + red_bytes(nt);
+}
+template <typename T>
+inline size_t smem_streamed(int nf, int na, int nt, bool scr_in_smem) {
+  const size_t v4 = 4 * sizeof(T);
+  return align_up(size_t(nf + 1) * v4, 16) + (scr_in_smem ? align_up(size_t(na) * v4, 16) : 0) +
+         red_bytes(nt);
+}
+
+constexpr int NODES_PER_THREAD = 4;  // free nodes owned per thread (registers)
+constexpr int MAX_THREADS = 1024;
+constexpr size_t SMEM_LIMIT = 232448;  // 227 KB opt-in per CTA
+
+// Arguments of the fused batched kernel.
+template <typename T>
+struct DrArgs {
+  const RveMeta* meta;
+  const FibD* fa;          // active fibers
+  const uint32_t* fij;     // packed endpoints i | j << 16 (nf = boundary zero slot)
+  const FibD* fb;          // boundary-to-boundary fibers
+  const uint16_t* csr;     // per free node: (active fiber << 1) | (node is endpoint j)
+  const uint32_t* ncsr;    // per free node: (local CSR begin << 8) | count
+  const float* ncap;       // per free node: STEP_CAP * min incident L0
+  const Work* work;
+  int32_t n_work;
+  const double* F;         // 9 per output index
+  double* sigma;           // 9 per output index
+  int32_t* iters;          // per output index (may be null)
+  int32_t* status;         // per output index (may be null)
+  T* state;                // 4 per state node (x, y, z, unused)
+  uint8_t* valid;          // per RVE: own state slot holds a solve
+  int32_t warm_start;
+  // streamed bins: per-solve scratch in global memory (Work::scr_off)
+  T* gP0;
+  T* gP1;
+  T* gSCR;
+  double tol;
+  int32_t max_iter;
+  int32_t check_every;
+  double damping;          // > 0 fixed, <= 0 adaptive
+};
+
+}  // namespace rvegpu
+
+// ---------------------------------------------------------------- host side
+#include <string>
+#include <vector>
+
+#include "rve.h"
+
+namespace rvegpu {
+
+// Per-thread error message behind rve_last_error().
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+// Host copy of one RVE's processed topology (after pruning/renumbering).
+struct HostTopology {
+  std::vector<RveMeta> meta;
+  std::vector<FibD> fa, fb;
+  std::vector<uint32_t> fij;
+  std::vector<uint16_t> csr;
+  std::vector<uint32_t> ncsr;
+  std::vector<float> ncap;
+  std::vector<int32_t> free_node_id;  // original RVE-local id of each free node
+  std::vector<int64_t> node_off_in;   // input node offsets (position export)
+  std::vector<double> X_in;           // input coordinates (position export)
+  int64_t pruned_fibers = 0;
+};
+
+// Validate, prune and lay out the input networks.  Returns RVE_OK or RVE_EINVAL.
+int build_topology(int64_t n_rve, const int64_t* node_off, const double* X, const int64_t* fiber_off,
+                   const int32_t* conn, const double* L0, const double* EA, const double* B,
+                   const uint8_t* is_boundary, const double* V0, HostTopology& out);
+
+}  // namespace rvegpu

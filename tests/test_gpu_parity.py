@@ -1,0 +1,280 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars (sigma, relative Frobenius error against the oracle):
+  mixed precision (FP32 forces, FP64 sums)  <= 1e-4
+  FP64 batched and plain FP64 paths         <= 1e-10 on the 6^3 RVE at
+                                              R_rel 1e-13, <= 1e-8 elsewhere
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import rvegen
+from oracle.newton import solve, solve_network
+from tests import nets as tnets
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def rve():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2306_09427_gb300 as rve
+    return rve
+
+
+def _F(F):
+    import torch
+    return torch.tensor(np.asarray(F).reshape(-1, 9), dtype=torch.float64, device="cuda:0")
+
+
+def gpu_solve(rve, nets, F, precision, tol, max_iter=0, **opts):
+    b = rve.RveBatch(rvegen.pack(nets), precision=precision, tol=tol, **opts)
+    s, it, st = b.solve(_F(F), max_iter=max_iter)
+    out = s.cpu().numpy().reshape(-1, 3, 3), it.cpu().numpy(), st.cpu().numpy()
+    b.close()
+    return out
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _golden(name):
+    path = os.path.join(HERE, "golden", f"oracle_{name}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not generated")
+    return json.load(open(path))["rows"]
+
+
+# ----------------------------------------------------------------- config 1
+
+def test_single_rve_all_paths(rve):
+    nets, F = rvegen.config_single()
+    ref = solve_network(nets[0], F[0], tol=1e-13).sigma
+    for prec, tol, bound in ((rve.RVE_PREC_BATCHED_F64, 1e-13, 1e-10), (rve.RVE_PREC_PLAIN_F64, 1e-13, 1e-10),
+                             (rve.RVE_PREC_MIXED, 1e-6, 1e-4)):
+        s, it, st = gpu_solve(rve, nets, F, prec, tol)
+        assert st[0] == rve.RVE_STATUS_CONVERGED
+        assert rel(s[0], ref) <= bound, (prec, rel(s[0], ref))
+
+
+# ------------------------------------------------ small batches, oracle live
+
+def _small_batch(count=12, seed=0):
+    nets, Fs = [], []
+    for k in range(count):
+        st = rvegen.Stream(1000 + seed * 100 + k)
+        n = 4 + k % 3
+        p = 0.55 + 0.1 * (k % 4)
+        net = rvegen.grid_network(n, p, st, EA="lognormal" if k % 2 else 1.0, B=[5.0, 10.0, 20.0][k % 3])
+        nets.append(net)
+        Fs.append(rvegen.random_F(st))
+    return nets, np.stack(Fs)
+
+
+@pytest.fixture(scope="module")
+def small_case():
+    nets, Fs = _small_batch()
+    refs = np.stack([solve_network(n, F, tol=1e-12).sigma for n, F in zip(nets, Fs)])
+    return nets, Fs, refs
+
+
+def test_small_batch_mixed(rve, small_case):
+    nets, Fs, refs = small_case
+    s, it, st = gpu_solve(rve, nets, Fs, rve.RVE_PREC_MIXED, 1e-6)
+    assert (st == rve.RVE_STATUS_CONVERGED).all()
+    errs = [rel(s[k], refs[k]) for k in range(len(nets))]
+    assert max(errs) <= 1e-4, errs
+
+
+def test_small_batch_fp64(rve, small_case):
+    nets, Fs, refs = small_case
+    s, it, st = gpu_solve(rve, nets, Fs, rve.RVE_PREC_BATCHED_F64, 1e-12)
+    assert (st == rve.RVE_STATUS_CONVERGED).all()
+    errs = [rel(s[k], refs[k]) for k in range(len(nets))]
+    assert max(errs) <= 1e-8, errs
+
+
+def test_plain_matches_batched_fp64(rve, small_case):
+    nets, Fs, refs = small_case
+    sb, _, _ = gpu_solve(rve, nets[:4], Fs[:4], rve.RVE_PREC_BATCHED_F64, 1e-12)
+    sp, _, stp = gpu_solve(rve, nets[:4], Fs[:4], rve.RVE_PREC_PLAIN_F64, 1e-12)
+    assert (stp == rve.RVE_STATUS_CONVERGED).all()
+    for k in range(4):
+        assert rel(sp[k], refs[k]) <= 1e-8
+        assert rel(sp[k], sb[k]) <= 1e-8
+
+
+def test_fixed_damping_converges_to_same_state(rve, small_case):
+    nets, Fs, refs = small_case
+    s, it, st = gpu_solve(rve, nets[:6], Fs[:6], rve.RVE_PREC_MIXED, 1e-6, damping=0.05)
+    for k in range(6):
+        if st[k] == rve.RVE_STATUS_CONVERGED:
+            assert rel(s[k], refs[k]) <= 1e-4
+
+
+# --------------------------------------- full-size uniform batch (1024 x 10^3)
+
+def test_uniform_full_batch_sampled(rve):
+    rows = _golden("uniform_10")
+    nets, Fs = rvegen.config_uniform(1024)
+    s, it, st = gpu_solve(rve, nets, Fs, rve.RVE_PREC_MIXED, 1e-6)
+    assert (st == rve.RVE_STATUS_CONVERGED).mean() >= 0.999
+    for r in rows:
+        if r["converged"]:
+            k = r["index"]
+            assert st[k] == rve.RVE_STATUS_CONVERGED
+            assert rel(s[k], np.array(r["sigma"]).reshape(3, 3)) <= 1e-4, (k, rel(s[k], np.array(r["sigma"]).reshape(3, 3)))
+    # properties that hold at any size: symmetric stress, finite everywhere
+    assert np.isfinite(s).all()
+    assert np.abs(s - s.transpose(0, 2, 1)).max() <= 1e-12 * np.abs(s).max()
+
+
+def test_uniform_fp64_sampled(rve):
+    rows = [r for r in _golden("uniform_10") if r["converged"]][:6]
+    nets, Fs = rvegen.config_uniform(len(rows))
+    s, it, st = gpu_solve(rve, nets, Fs, rve.RVE_PREC_BATCHED_F64, 1e-12)
+    for r in rows:
+        k = r["index"]
+        assert st[k] == rve.RVE_STATUS_CONVERGED
+        assert rel(s[k], np.array(r["sigma"]).reshape(3, 3)) <= 1e-8
+
+
+# ------------------------------------------------- uneven batch, all bins
+
+def test_uneven_batch(rve):
+    rows = _golden("uneven")
+    n = max(r["index"] for r in rows) + 1
+    nets, Fs = rvegen.config_uneven(n)
+    for prec, tol, bound in ((rve.RVE_PREC_MIXED, 1e-6, 1e-4), (rve.RVE_PREC_BATCHED_F64, 1e-11, 1e-7)):
+        s, it, st = gpu_solve(rve, nets, Fs, prec, tol)
+        for r in rows:
+            if not r["converged"]:
+                continue
+            k = r["index"]
+            assert st[k] == rve.RVE_STATUS_CONVERGED, (prec, k)
+            assert rel(s[k], np.array(r["sigma"]).reshape(3, 3)) <= bound, (prec, k, r["side"])
+
+
+# ------------------------------------------------------------- edge cases
+
+def test_rigid_rotation_zero_stress_zero_iterations(rve):
+    net = tnets.lattice(6, p=0.6, jitter=0.3, seed=5)
+    from scipy.spatial.transform import Rotation
+    R = Rotation.from_rotvec([0.4, -0.2, 0.9]).as_matrix()
+    for prec in (rve.RVE_PREC_MIXED, rve.RVE_PREC_BATCHED_F64, rve.RVE_PREC_PLAIN_F64):
+        s, it, st = gpu_solve(rve, [net], R[None], prec, 1e-8)
+        assert st[0] == rve.RVE_STATUS_CONVERGED and it[0] == 0
+        assert np.abs(s[0]).max() < 1e-12
+
+
+def test_degenerate_rves_in_a_batch(rve):
+    # 0: no fibers; 1: boundary-only fibers (sigma exact); 2: a normal RVE;
+    # 3: inverted F (det < 0) -> NONFINITE without disturbing the others
+    empty = rvegen.Network(X=np.array([[0.0, 0, 0], [1, 0, 0]]), conn=np.zeros((0, 2), np.int32), L0=np.zeros(0),
+                           EA=np.zeros(0), B=np.zeros(0), is_boundary=np.array([1, 1], np.uint8))
+    Xb = np.array([[-0.5, -0.5, 0.0], [0.5, 0.5, 0.0], [0.5, -0.5, 0.3]])
+    cb = np.array([[0, 1], [1, 2]], np.int32)
+    bonly = rvegen.Network(X=Xb, conn=cb, L0=np.linalg.norm(Xb[cb[:, 1]] - Xb[cb[:, 0]], axis=1), EA=np.array([1.0, 2.0]),
+                           B=np.array([10.0, 0.0]), is_boundary=np.ones(3, np.uint8))
+    normal = tnets.lattice(5, p=0.7, jitter=0.3, seed=3)
+    F = np.array([[1.05, 0.02, 0.0], [0.0, 0.98, 0.01], [0.03, 0.0, 1.1]])
+    Finv = np.diag([1.0, 1.0, -1.0])
+    nets = [empty, bonly, normal, normal]
+    Fs = np.stack([F, F, F, Finv])
+    for prec in (rve.RVE_PREC_MIXED, rve.RVE_PREC_BATCHED_F64, rve.RVE_PREC_PLAIN_F64):
+        s, it, st = gpu_solve(rve, nets, Fs, prec, 1e-6 if prec == rve.RVE_PREC_MIXED else 1e-10)
+        assert st[0] == rve.RVE_STATUS_EMPTY and np.abs(s[0]).max() == 0.0
+        ref1 = solve_network(bonly, F).sigma
+        assert st[1] == rve.RVE_STATUS_EMPTY and rel(s[1], ref1) <= 1e-14
+        assert st[2] == rve.RVE_STATUS_CONVERGED
+        assert rel(s[2], solve_network(normal, F).sigma) <= (1e-4 if prec == rve.RVE_PREC_MIXED else 1e-8)
+        assert st[3] == rve.RVE_STATUS_NONFINITE and np.isnan(s[3]).all()
+
+
+def test_max_iter_status(rve):
+    nets, Fs = rvegen.config_uniform(3, side=6)
+    s, it, st = gpu_solve(rve, nets, Fs, rve.RVE_PREC_MIXED, 1e-12, max_iter=7)
+    assert (st == rve.RVE_STATUS_MAX_ITER).all() and (it == 7).all()
+    assert np.isfinite(s).all()
+
+
+def test_batch_independence_and_determinism(rve):
+    nets, Fs = rvegen.config_uneven(40, side_hi=12)
+    s_all, _, _ = gpu_solve(rve, nets, Fs, rve.RVE_PREC_MIXED, 1e-6)
+    s_again, _, _ = gpu_solve(rve, nets, Fs, rve.RVE_PREC_MIXED, 1e-6)
+    assert np.array_equal(s_all, s_again)
+    for k in (0, 7, 39):
+        s1, _, _ = gpu_solve(rve, [nets[k]], Fs[k:k + 1], rve.RVE_PREC_MIXED, 1e-6)
+        assert np.array_equal(s1[0], s_all[k])
+
+
+def test_subset_equals_full_and_host_equals_device(rve):
+    import torch
+    nets, Fs = rvegen.config_uneven(30, side_hi=10)
+    b = rve.RveBatch(rvegen.pack(nets), precision=rve.RVE_PREC_MIXED, tol=1e-6)
+    s, it, st = b.solve(_F(Fs))
+    ids = np.array([29, 3, 17, 8])
+    ss, its, sts = b.solve_subset(ids, _F(Fs[ids]))
+    assert torch.equal(ss, s[torch.as_tensor(ids, device=s.device)])
+    sh, ih, sth = b.solve_host(Fs)
+    assert np.array_equal(sh, s.cpu().numpy()) and np.array_equal(ih, it.cpu().numpy())
+    with pytest.raises(rve.RveError):
+        b.solve_subset(np.array([1, 1]), _F(Fs[:2]))
+    b.close()
+
+
+def test_warm_start(rve):
+    nets, Fs = rvegen.config_uniform(8, side=8)
+    b = rve.RveBatch(rvegen.pack(nets), precision=rve.RVE_PREC_MIXED, tol=1e-6, warm_start=1)
+    s1, it1, st1 = b.solve(_F(Fs))
+    s2, it2, st2 = b.solve(_F(Fs))
+    assert (it2.cpu().numpy() == 0).all()  # restarts at the converged state
+    assert np.array_equal(s1.cpu().numpy(), s2.cpu().numpy())
+    # a small increment converges faster from the previous state than from scratch
+    F2 = Fs + 0.002 * np.eye(3)
+    s3, it3, _ = b.solve(_F(F2))
+    b.reset_state()
+    s4, it4, _ = b.solve(_F(F2))
+    assert it3.sum() < it4.sum()
+    assert rel(s3.cpu().numpy(), s4.cpu().numpy()) <= 1e-4
+    x = b.positions(0, F2[0], nets[0].n_nodes)
+    assert x.shape == (nets[0].n_nodes, 3) and np.isfinite(x).all()
+    b.close()
+
+
+def test_tangent_fp64_matches_oracle(rve):
+    net = tnets.lattice(5, p=0.7, jitter=0.3, seed=9, B=8.0)
+    F = rvegen.random_F(rvegen.Stream(31))
+    sig_o, D_o = __import__("oracle").dsigma_dF(net.X, net.conn, net.L0, net.EA, net.B, net.is_boundary, F)
+    b = rve.RveBatch(rvegen.pack([net]), precision=rve.RVE_PREC_BATCHED_F64, tol=1e-12)
+    sig, D, st = b.tangent(_F(F[None]))
+    D = D.cpu().numpy().reshape(9, 9)
+    assert int(st[0]) == rve.RVE_STATUS_CONVERGED
+    assert rel(sig.cpu().numpy().reshape(3, 3), sig_o) <= 1e-9
+    assert rel(D, D_o) <= 1e-5, rel(D, D_o)
+    # rows ij and ji agree (sigma symmetric)
+    for i in range(3):
+        for j in range(3):
+            assert np.allclose(D[3 * i + j], D[3 * j + i], rtol=0, atol=1e-9 * np.abs(D).max())
+    b.close()
+
+
+def test_tangent_mixed_precision_accuracy(rve):
+    net = tnets.lattice(5, p=0.7, jitter=0.3, seed=9, B=8.0)
+    F = rvegen.random_F(rvegen.Stream(31))
+    sig_o, D_o = __import__("oracle").dsigma_dF(net.X, net.conn, net.L0, net.EA, net.B, net.is_boundary, F)
+    b = rve.RveBatch(rvegen.pack([net]), precision=rve.RVE_PREC_MIXED, tol=1e-7)
+    sig, D, st = b.tangent(_F(F[None]))
+    assert rel(sig.cpu().numpy().reshape(3, 3), sig_o) <= 1e-4
+    # FP32 stresses differenced over 2h = 2e-4: a few percent is the expected floor
+    assert rel(D.cpu().numpy().reshape(9, 9), D_o) <= 5e-2
+    b.close()
