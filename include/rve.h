@@ -160,6 +160,36 @@ int rve_solve_host(rve_batch* b, const double* F, double tol, int32_t max_iter, 
                    int32_t* iters, int32_t* status);
 
 /*
+ * Allocation-free plain FP64 solve of RVE r of an existing batch.  The
+ * paper has no counterpart; this call exists for callers that must not
+ * allocate device memory while they solve (device memory carved up once at
+ * start-up by a caching allocator or a fixed budget, where cudaMalloc may
+ * fail or synchronise the whole device; loops whose latency limits forbid
+ * allocator calls).  It runs the kernels of the RVE_PREC_PLAIN_F64 path
+ * with their working buffers in a fixed scratch array compiled into the
+ * library (about 2.3 MB held on every GPU that loads the library, until
+ * the process exits), and calls no allocator: no cudaMalloc/cudaFree, no
+ * library allocation.
+ *   r         RVE index; its active fibers must not exceed
+ *             RVE_NOALLOC_MAX_ACTIVE_FIBERS and its free nodes
+ *             RVE_NOALLOC_MAX_FREE_NODES, else RVE_EINVAL with a message.
+ *   F         device, 9 doubles; sigma device, 9 doubles;
+ *   iters, status   device, one int32 each (may be NULL).
+ *   tol <= 0, max_iter <= 0 keep the batch options.
+ * Always starts from h = 0 and leaves the batch's warm-start state alone.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  All calls, on any batch, share the one array and the
+ * call returns only after the solve's last convergence check: calls that
+ * overlap on the GPU (from several host threads) race and must be
+ * serialised by the caller.
+ */
+#define RVE_NOALLOC_MAX_ACTIVE_FIBERS 16384
+#define RVE_NOALLOC_MAX_FREE_NODES 8192
+int rve_solve_plain_noalloc(rve_batch* b, int64_t r, const double* F, double tol, int32_t max_iter,
+                            double* sigma, int32_t* iters, int32_t* status, void* stream);
+
+/*
  * Stress and stress tangent: sigma(F) and the central-difference
  * derivative dsigma_ij/dF_kl = (sigma_ij(F + h E_kl) - sigma_ij(F - h E_kl)) / 2h,
  * E_kl = e_k (x) e_l, nine directions, i.e. 18 perturbed solves per RVE

@@ -10,6 +10,7 @@ from ._lib import (RVE_EADMIT, RVE_ECUDA, RVE_EINVAL, RVE_ENOMEM, RVE_OK, RVE_PR
                    RVE_STATUS_MAX_ITER, RVE_STATUS_NONFINITE, RveBatch, RveError, lib, lib_path,
                    rve_batch_create, rve_batch_destroy, rve_batch_get_info, rve_batch_get_sizes,
                    rve_get_positions, rve_last_error, rve_options_default, rve_reset_state,
-                   rve_set_options, rve_solve, rve_solve_host, rve_solve_subset, rve_tangent)
+                   rve_set_options, rve_solve, rve_solve_host, rve_solve_plain_noalloc, rve_solve_subset,
+                   rve_tangent, RVE_NOALLOC_MAX_ACTIVE_FIBERS, RVE_NOALLOC_MAX_FREE_NODES)
 
 __all__ = [n for n in dir() if n.startswith(("rve_", "RVE_", "Rve"))] + ["lib", "lib_path"]

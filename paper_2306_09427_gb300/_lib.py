@@ -48,6 +48,8 @@ rve_set_options = _sig("rve_set_options", C.c_int, [_P, C.POINTER(rve_options)])
 rve_solve = _sig("rve_solve", C.c_int, [_P, _P, _D, _I32, _P, _P, _P, _P])
 rve_solve_subset = _sig("rve_solve_subset", C.c_int, [_P, _P, _I64, _P, _D, _I32, _P, _P, _P, _P])
 rve_solve_host = _sig("rve_solve_host", C.c_int, [_P, _P, _D, _I32, _P, _P, _P])
+rve_solve_plain_noalloc = _sig("rve_solve_plain_noalloc", C.c_int, [_P, _I64, _P, _D, _I32, _P, _P, _P, _P])
+RVE_NOALLOC_MAX_ACTIVE_FIBERS, RVE_NOALLOC_MAX_FREE_NODES = 16384, 8192
 rve_tangent = _sig("rve_tangent", C.c_int, [_P, _P, _D, _D, _I32, _P, _P, _P, _P])
 rve_reset_state = _sig("rve_reset_state", C.c_int, [_P, _P, _I64])
 rve_batch_get_info = _sig("rve_batch_get_info", C.c_int, [_P, C.POINTER(rve_batch_info)])
@@ -176,6 +178,21 @@ class RveBatch:
         status = np.empty(self.n_rve, np.int32)
         _check(rve_solve_host(self.h, _ptr(F), tol, max_iter, _ptr(sigma), _ptr(iters), _ptr(status)),
                "rve_solve_host")
+        return sigma, iters, status
+
+    def solve_plain_noalloc(self, r: int, F, tol: float = 0.0, max_iter: int = 0, sigma=None, iters=None,
+                            status=None, stream=None):
+        """Plain FP64 solve of RVE r without any device allocation (see include/rve.h).
+        F: CUDA float64 tensor of 9; outputs are CUDA tensors of 9, 1 and 1 elements."""
+        import torch
+        if sigma is None:
+            sigma = torch.empty(9, dtype=torch.float64, device=F.device)
+        if iters is None:
+            iters = torch.empty(1, dtype=torch.int32, device=F.device)
+        if status is None:
+            status = torch.empty(1, dtype=torch.int32, device=F.device)
+        _check(rve_solve_plain_noalloc(self.h, r, _ptr(F), tol, max_iter, _ptr(sigma), _ptr(iters), _ptr(status),
+                                       _stream_handle(stream)), "rve_solve_plain_noalloc")
         return sigma, iters, status
 
     def tangent(self, F, h: float = 1e-4, tol: float = 0.0, max_iter: int = 0, stream=None):

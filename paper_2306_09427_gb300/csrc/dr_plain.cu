@@ -431,3 +431,176 @@ int plain_solve_one(rve_batch* b, int r, int out, const double* F, double tol, i
 }
 
 }  // namespace rvegpu
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the plain FP64 solve.
+//
+// Some callers must not allocate device memory while they solve: programs
+// whose device memory is carved up once at start-up (a caching allocator
+// or a fixed budget shared with other work, where a cudaMalloc may fail or
+// implicitly synchronise the device and stall every stream) and loops with
+// latency limits that forbid allocator calls.  rve_solve_plain_noalloc
+// serves them: it solves one RVE of an existing batch with the plain FP64
+// kernels above, taking its working buffers from a fixed scratch array
+// compiled into this library instead of the batch's own scratch.  The
+// array is a file-scope __device__ variable, so every GPU that loads the
+// library holds it (about 2.3 MB) until the process exits.
+#include <mutex>
+
+namespace rvegpu {
+namespace {
+
+constexpr int NOALLOC_NA = RVE_NOALLOC_MAX_ACTIVE_FIBERS;
+constexpr int NOALLOC_NF = RVE_NOALLOC_MAX_FREE_NODES;
+
+constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
+constexpr size_t noalloc_bytes() {
+  return 3 * na_align(sizeof(dvec4) * size_t(NOALLOC_NA + 1)) + 3 * na_align(sizeof(dvec4) * size_t(NOALLOC_NF + 1)) +
+         na_align(sizeof(double) * 4 * size_t(NOALLOC_NF / PT + 2)) + na_align(sizeof(double) * 32) +
+         na_align(sizeof(double) * 12 * size_t(NOALLOC_NA / PT + 2));
+}
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[noalloc_bytes()];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};
+
+// pl_finish without touching the batch's warm-start flags
+__global__ void pl_finish_noalloc(const RveMeta* meta, int r, int nblk, const double* F, int it, int status,
+                                  double* sigma, int32_t* iters, int32_t* st, PlainBufs B) {
+  __shared__ double comp[6];
+  const RveMeta M = meta[r];
+  if (threadIdx.x < 6) {
+    double s = B.res[1 + 2 * threadIdx.x], c = B.res[2 + 2 * threadIdx.x];
+    for (int b = 0; b < nblk; ++b) {
+      double tt, ee;
+      two_sum(s, B.sig[12 * b + 2 * threadIdx.x], tt, ee);
+      s = tt;
+      c += ee + B.sig[12 * b + 2 * threadIdx.x + 1];
+    }
+    comp[threadIdx.x] = s + c;
+  }
+  __syncthreads();
+  const double detF = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                      F[2] * (F[3] * F[7] - F[4] * F[6]);
+  const bool badF = !(detF > 0.0) || !(detF < 1e300);
+  if (threadIdx.x < 9) {
+    const int i = threadIdx.x / 3, j = threadIdx.x % 3;
+    const int idx = (i == j) ? i : 6 - i - j;
+    sigma[threadIdx.x] = badF ? __longlong_as_double(0x7ff8000000000000ll) : comp[idx] / (detF * M.V0);
+  }
+  if (threadIdx.x == 0) {
+    if (iters) *iters = it;
+    if (st) *st = badF ? RVE_STATUS_NONFINITE : status;
+  }
+}
+
+}  // namespace
+}  // namespace rvegpu
+
+extern "C" int rve_solve_plain_noalloc(rve_batch* b, int64_t r, const double* F, double tol, int32_t max_iter,
+                                       double* sigma, int32_t* iters, int32_t* status, void* stream) {
+  using namespace rvegpu;
+  if (!b || !F || !sigma) return fail(RVE_EINVAL, "batch, F and sigma are required");
+  if (r < 0 || r >= b->n_rve) return fail(RVE_EINVAL, "RVE index out of range");
+  const RveMeta& M = b->topo.meta[r];
+  if (M.na > NOALLOC_NA || M.nf > NOALLOC_NF)
+    return fail(RVE_EINVAL, "RVE " + std::to_string(r) + " has " + std::to_string(M.na) + " active fibers and " +
+                                std::to_string(M.nf) + " free nodes; rve_solve_plain_noalloc handles at most " +
+                                std::to_string(NOALLOC_NA) + " and " + std::to_string(NOALLOC_NF));
+  if (!(tol > 0.0)) tol = b->opt.tol;
+  if (max_iter <= 0) max_iter = b->opt.max_iter;
+  RVE_CUDA_TRY(cudaSetDevice(b->device));
+  if (b->device < 0 || b->device >= 64) return fail(RVE_EINVAL, "device ordinal too large");
+  void* base_v = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[b->device]) {
+      void* p = nullptr;
+      RVE_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      g_noalloc_addr[b->device] = p;
+    }
+    base_v = g_noalloc_addr[b->device];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* base = static_cast<unsigned char*>(base_v);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char* p = base + off;
+    off += na_align(bytes);
+    return p;
+  };
+  const int na = M.na, nf = M.nf;
+  PlainBufs B;
+  B.P0 = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(na + 1)));
+  B.P1 = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(na + 1)));
+  B.SCR = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(na + 1)));
+  B.H = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(nf + 1)));
+  B.V = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(nf + 1)));
+  B.Fn = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(nf + 1)));
+  const int nblk_n = (nf + PT - 1) / PT, nblk_a = (na + PT - 1) / PT;
+  B.part = reinterpret_cast<double*>(take(sizeof(double) * 4 * size_t(nblk_n + 1)));
+  B.res = reinterpret_cast<double*>(take(sizeof(double) * 32));
+  B.sig = reinterpret_cast<double*>(take(sizeof(double) * 12 * size_t(nblk_a + 1)));
+  if (off > noalloc_bytes()) return fail(RVE_EINVAL, "internal: no-alloc scratch layout overflow");
+  // the array keeps the previous call's contents: clear what is accumulated
+  RVE_CUDA_TRY(cudaMemsetAsync(B.part, 0, sizeof(double) * 4 * size_t(nblk_n + 1), s));
+  RVE_CUDA_TRY(cudaMemsetAsync(B.res, 0, sizeof(double) * 32, s));
+
+  pl_setup<<<1, PT, 0, s>>>(b->d_meta, int(r), b->d_fa, b->d_fij, b->d_fb, F, 0, nullptr, nullptr, 0, B);
+  RVE_CUDA_TRY(cudaGetLastError());
+  RVE_CUDA_TRY(cudaMemcpyAsync(b->h_pl, B.res, 14 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  RVE_CUDA_TRY(cudaStreamSynchronize(s));
+  const double detF = b->h_pl[13];
+  const bool badF = !(detF > 0.0) || !(detF < 1e300);
+  const double thr = std::fmax(tol * std::sqrt(b->h_pl[0]), ABS_FLOOR * M.sum_EA);
+  const double thr2 = thr * thr;
+  const int K = b->opt.check_every;
+  const bool adaptive = !(b->opt.damping > 0.0);
+  double c = adaptive ? DAMP_C0 : b->opt.damping;
+  double alpha = (2.0 - c) / (2.0 + c), beta = 2.0 / (2.0 + c);
+  bool have_pre = false;
+  int it = 0, st = RVE_STATUS_EMPTY;
+  if (nf > 0 && !badF) {
+    st = RVE_STATUS_MAX_ITER;
+    for (;; ++it) {
+      pl_fiber<<<(na + PT - 1) / PT, PT, 0, s>>>(na, B);
+      const bool check = (it % K == 0) || it >= max_iter;
+      const int pre_it = adaptive && ((it + 1) % K == 0);
+      if (!check) {
+        pl_node<<<nblk_n, PT, 0, s>>>(b->d_meta, int(r), b->d_csr, b->d_ncsr, b->d_ncap, alpha, beta, pre_it, B);
+      } else {
+        pl_node_check<<<nblk_n, PT, 0, s>>>(b->d_meta, int(r), b->d_csr, b->d_ncsr, B);
+        pl_reduce<<<1, PT, 0, s>>>(nblk_n, B);
+        RVE_CUDA_TRY(cudaGetLastError());
+        RVE_CUDA_TRY(cudaMemcpyAsync(b->h_pl, B.res + 16, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        RVE_CUDA_TRY(cudaStreamSynchronize(s));
+        const double pre = b->h_pl[0], pm = b->h_pl[1], r2 = b->h_pl[2], post = b->h_pl[3];
+        if (!(r2 < 1e300)) {
+          st = RVE_STATUS_NONFINITE;
+          break;
+        }
+        if (r2 <= thr2) {
+          st = RVE_STATUS_CONVERGED;
+          break;
+        }
+        if (it >= max_iter) break;
+        if (adaptive && have_pre && pm > 0.0) {
+          const double lam = -(post - pre) / pm;
+          if (lam > 0.0) {
+            c = std::fmin(2.0 * std::sqrt(lam), DAMP_C_MAX);
+            alpha = (2.0 - c) / (2.0 + c);
+            beta = 2.0 / (2.0 + c);
+          }
+        }
+        pl_node_apply<<<nblk_n, PT, 0, s>>>(b->d_meta, int(r), b->d_ncap, alpha, beta, pre_it, B);
+      }
+      RVE_CUDA_TRY(cudaGetLastError());
+      have_pre = pre_it != 0;
+    }
+  }
+  if (na > 0) pl_sigma<<<nblk_a, PT, 0, s>>>(na, B);
+  pl_finish_noalloc<<<1, 32, 0, s>>>(b->d_meta, int(r), na > 0 ? nblk_a : 0, F, it, st, sigma, iters, status, B);
+  RVE_CUDA_TRY(cudaGetLastError());
+  return RVE_OK;
+}

@@ -1,0 +1,58 @@
+"""rve_solve_plain_noalloc: the plain FP64 solve for callers that cannot
+allocate device memory while they solve (memory carved up once at start-up,
+or allocator calls forbidden in the loop).  Its output must match the
+regular plain path, rve_solve with RVE_PREC_PLAIN_F64, call after call."""
+import numpy as np
+import pytest
+
+import rvegen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rve():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2306_09427_gb300 as rve
+    return rve
+
+
+def _F(F):
+    import torch
+    return torch.tensor(np.asarray(F).reshape(-1, 9), dtype=torch.float64, device="cuda:0")
+
+
+def test_noalloc_matches_plain_path_on_two_calls(rve):
+    import torch
+    nets, Fs = rvegen.config_uniform(3, side=7)
+    b = rve.RveBatch(rvegen.pack(nets), precision=rve.RVE_PREC_PLAIN_F64, tol=1e-10)
+    Fd = _F(Fs)
+    s_ref, it_ref, st_ref = b.solve(Fd)
+    torch.cuda.synchronize()
+    s_ref, it_ref, st_ref = s_ref.cpu().numpy(), it_ref.cpu().numpy(), st_ref.cpu().numpy()
+    assert (st_ref == rve.RVE_STATUS_CONVERGED).all()
+    for call in range(2):
+        for r in range(3):
+            s, it, st = b.solve_plain_noalloc(r, Fd[r].contiguous())
+            torch.cuda.synchronize()
+            s = s.cpu().numpy()
+            assert int(st[0]) == rve.RVE_STATUS_CONVERGED
+            assert int(it[0]) == int(it_ref[r])
+            err = np.linalg.norm(s - s_ref[r]) / np.linalg.norm(s_ref[r])
+            assert err <= 1e-10, (call, r, err)
+    b.close()
+
+
+def test_noalloc_rejects_rves_over_the_limit(rve):
+    net = rvegen.grid_network(20, 1.0, rvegen.Stream(1))
+    b = rve.RveBatch(rvegen.pack([net]), precision=rve.RVE_PREC_PLAIN_F64)
+    nf, na, _ = b.sizes()
+    assert na[0] > rve.RVE_NOALLOC_MAX_ACTIVE_FIBERS
+    with pytest.raises(rve.RveError) as e:
+        b.solve_plain_noalloc(0, _F(np.eye(3))[0].contiguous())
+    assert e.value.code == rve.RVE_EINVAL and "at most" in str(e.value)
+    b.close()
