@@ -20,7 +20,8 @@ RVE_PREC_PLAIN_F64, RVE_PREC_MIXED, RVE_PREC_BATCHED_F64 = 0, 1, 2
 class rve_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("check_every", C.c_int32),
                 ("precision", C.c_int32), ("warm_start", C.c_int32), ("damping", C.c_double),
-                ("threads", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("threads", C.c_int32), ("reserved0", C.c_int32), ("sigma_tol", C.c_double),
+                ("reserved", C.c_int32 * 4)]
 
 
 class rve_batch_info(C.Structure):

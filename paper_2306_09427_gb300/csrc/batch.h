@@ -25,9 +25,11 @@ struct Bin {
   int per_sm = 1; // CTAs per SM the footprint allows (bin key)
   size_t smem = 0;
   std::vector<Work> work;
-  Work* d_work = nullptr;
+  Work* d_work = nullptr;    // canonical order
+  Work* d_sorted = nullptr;  // longest-first order written before each launch (bins up to LPT_MAX)
   int n = 0;
 };
+constexpr int LPT_MAX = 16384;  // bins up to this size are sorted on the device before launch
 
 // Launch configuration chosen for one RVE.
 struct BinKey {
@@ -44,16 +46,18 @@ struct PathState {
   std::vector<BinKey> key_of;   // per RVE
   std::vector<Bin> bins;        // all-RVE solve
   std::vector<Bin> tan_bins;    // tangent: 18 perturbed solves per RVE
-  void* d_state = nullptr;      // 4 T per free node (fluctuation h)
+  void* d_state = nullptr;      // 4 doubles per free node (fluctuation h, FP64 for both paths)
   uint8_t* d_valid = nullptr;   // per RVE: state holds a previous solve
+  int32_t* d_last_iters = nullptr;  // per RVE: iterations of its last solve (scheduling cost)
   void* d_gP0 = nullptr;        // streamed-bin scratch (4 T per active fiber)
   void* d_gP1 = nullptr;
   void* d_gSCR = nullptr;
-  void* d_tan_state = nullptr;  // 18 x 4 T per free node
+  void* d_tan_state = nullptr;  // 18 x 4 doubles per free node
   void* d_tan_g[3] = {};        // streamed-bin scratch of the tangent directions
   std::vector<int> bin_of;      // per RVE: index into bins
   std::vector<Work> work_of;    // per RVE: its work item in the all-RVE solve
   Work* d_sub_work = nullptr;   // subset solves
+  Work* d_sub_sorted = nullptr;
   size_t sub_cap = 0;
 };
 

@@ -64,6 +64,7 @@ int valid_options(const rve_options& o) {
     return fail(RVE_EINVAL, "unknown precision");
   if (o.warm_start != 0 && o.warm_start != 1) return fail(RVE_EINVAL, "warm_start must be 0 or 1");
   if (!std::isfinite(o.damping)) return fail(RVE_EINVAL, "damping must be finite");
+  if (!std::isfinite(o.sigma_tol)) return fail(RVE_EINVAL, "sigma_tol must be finite");
   if (o.threads != 0 && o.threads != 64 && o.threads != 128 && o.threads != 256 && o.threads != 512 &&
       o.threads != 1024)
     return fail(RVE_EINVAL, "threads must be 0, 64, 128, 256, 512 or 1024");
@@ -72,7 +73,7 @@ int valid_options(const rve_options& o) {
 
 // Launch configuration of one RVE in the fused kernel.
 template <typename T>
-int choose_key(int nf, int na, int threads, BinKey& k) {
+int choose_key(int nf, int na, int csr_len, int threads, BinKey& k) {
   if (nf > 4 * MAX_THREADS) return fail(RVE_EINVAL, "the batched path holds at most 4096 free nodes per RVE");
   int nt;
   if (threads > 0) {
@@ -89,7 +90,7 @@ int choose_key(int nf, int na, int threads, BinKey& k) {
   };
   int npt = npt_of(nf, nt);
   const size_t budget = SMEM_LIMIT - 1024;
-  size_t sm = smem_resident<T>(nf, na, nt);
+  size_t sm = smem_resident<T>(nf, na, csr_len, nt);
   int mode = 0;
   if (sm > budget) {
     nt = 1024;
@@ -125,7 +126,67 @@ int upload_bins(rve_batch* b, std::vector<Bin>& bins) {
   for (Bin& bin : bins) {
     bin.n = int(bin.work.size());
     TRY(upload(b, &bin.d_work, bin.work));
+    if (bin.n > 0 && bin.n <= LPT_MAX) TRY(upload(b, &bin.d_sorted, bin.work));
   }
+  return RVE_OK;
+}
+
+// Longest-first order of a bin's work items by learned cost: active fibers x
+// (iterations of the RVE's last solve + 1); ties keep the canonical order.
+// One CTA, bitonic sort of 64-bit keys (cost << 17 | reversed position).
+__global__ void lpt_sort(const Work* __restrict__ in, Work* __restrict__ out, int n, const RveMeta* __restrict__ meta,
+                         const int32_t* __restrict__ last_iters) {
+  extern __shared__ unsigned long long key[];
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    unsigned long long k = 0ull;
+    if (i < n) {
+      const int r = in[i].rve;
+      const unsigned long long cost =
+          static_cast<unsigned long long>(meta[r].na) * static_cast<unsigned long long>(max(last_iters[r], 0) + 1);
+      k = (cost << 17) | static_cast<unsigned long long>((1 << 17) - 1 - i);
+    }
+    key[i] = k;
+  }
+  __syncthreads();
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long a = key[i], c = key[ixj];
+          const bool desc = (i & k) == 0;
+          if (desc ? (a < c) : (a > c)) {
+            key[i] = c;
+            key[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    out[i] = in[(1 << 17) - 1 - static_cast<int>(key[i] & 0x1ffffull)];
+}
+
+int launch_sorted(rve_batch* b, const Bin& bin, cudaStream_t s, const int32_t* last_iters, Bin& use) {
+  use = bin;
+  if (!bin.d_sorted || bin.n <= 1 || bin.n > LPT_MAX) return RVE_OK;
+  int n2 = 1;
+  while (n2 < bin.n) n2 <<= 1;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  RVE_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 64 && !attr_set[dev]) {
+    RVE_CUDA_TRY(cudaFuncSetAttribute(lpt_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(LPT_MAX * sizeof(unsigned long long))));
+    attr_set[dev] = true;
+  }
+  lpt_sort<<<1, 1024, size_t(n2) * sizeof(unsigned long long), s>>>(bin.d_work, bin.d_sorted, bin.n, b->d_meta,
+                                                                     last_iters);
+  RVE_CUDA_TRY(cudaGetLastError());
+  use.d_work = bin.d_sorted;
   return RVE_OK;
 }
 
@@ -140,7 +201,7 @@ int ensure_path(rve_batch* b) {
   for (int64_t r = 0; r < n; ++r) {
     const RveMeta& M = b->topo.meta[r];
     BinKey k;
-    TRY(choose_key<T>(M.nf, M.na, b->opt.threads, k));
+    TRY(choose_key<T>(M.nf, M.na, M.csr_len, b->opt.threads, k));
     P.key_of[r] = k;
     size_t j = 0;
     while (j < keys.size() && !(keys[j] == k)) ++j;
@@ -157,9 +218,9 @@ int ensure_path(rve_batch* b) {
   for (int64_t r = 0; r < n; ++r) {
     if (P.key_of[r].mode == 0) continue;
     scr_of[r] = int32_t(scr_main);
-    scr_main += b->topo.meta[r].na;
+    scr_main += b->topo.meta[r].na + 1;  // + the zero slot
     scr_tan_of[r] = int32_t(scr_tan);
-    scr_tan += int64_t(N_DIRS) * b->topo.meta[r].na;
+    scr_tan += int64_t(N_DIRS) * (b->topo.meta[r].na + 1);
   }
   if (scr_tan > INT32_MAX) return fail(RVE_EINVAL, "streamed scratch exceeds 32-bit offsets");
   P.bins.clear();
@@ -179,7 +240,7 @@ int ensure_path(rve_batch* b) {
     for (int r : mem)
       for (int d = 0; d < N_DIRS; ++d)
         tb.work.push_back(Work{r, int32_t(d * n + r), int32_t(d * b->total_nf + b->topo.meta[r].node_off), 1,
-                               int32_t(scr_tan_of[r] + d * b->topo.meta[r].na), 0});
+                               int32_t(scr_tan_of[r] + d * (b->topo.meta[r].na + 1)), 0});
     P.bins.push_back(std::move(bin));
     P.tan_bins.push_back(std::move(tb));
   }
@@ -201,10 +262,12 @@ int ensure_path(rve_batch* b) {
     }
   TRY(upload_bins(b, P.bins));
   TRY(upload_bins(b, P.tan_bins));
-  TRY(dalloc(b, &P.d_state, sizeof(T) * 4 * size_t(std::max<int64_t>(b->total_nf, 1))));
-  RVE_CUDA_TRY(cudaMemset(P.d_state, 0, sizeof(T) * 4 * size_t(std::max<int64_t>(b->total_nf, 1))));
+  TRY(dalloc(b, &P.d_state, sizeof(double) * 4 * size_t(std::max<int64_t>(b->total_nf, 1))));
+  RVE_CUDA_TRY(cudaMemset(P.d_state, 0, sizeof(double) * 4 * size_t(std::max<int64_t>(b->total_nf, 1))));
   TRY(dalloc(b, reinterpret_cast<void**>(&P.d_valid), size_t(std::max<int64_t>(n, 1))));
   RVE_CUDA_TRY(cudaMemset(P.d_valid, 0, size_t(std::max<int64_t>(n, 1))));
+  TRY(dalloc(b, reinterpret_cast<void**>(&P.d_last_iters), sizeof(int32_t) * size_t(std::max<int64_t>(n, 1))));
+  RVE_CUDA_TRY(cudaMemset(P.d_last_iters, 0, sizeof(int32_t) * size_t(std::max<int64_t>(n, 1))));
   if (scr_main > 0) {
     TRY(dalloc(b, &P.d_gP0, sizeof(T) * 4 * size_t(scr_main)));
     TRY(dalloc(b, &P.d_gP1, sizeof(T) * 4 * size_t(scr_main)));
@@ -216,16 +279,23 @@ int ensure_path(rve_batch* b) {
 
 // Run a list of bins on `s`, concurrently on side streams when there are several.
 template <typename T>
+int run_one(rve_batch* b, const Bin& bin, const DrArgs<T>& a, cudaStream_t s) {
+  Bin use;
+  TRY(launch_sorted(b, bin, s, a.last_iters, use));
+  return launch_bin(a, use, s);
+}
+
+template <typename T>
 int run_bins(rve_batch* b, const std::vector<Bin>& bins, const DrArgs<T>& a, cudaStream_t s) {
   std::vector<const Bin*> live;
   for (const Bin& x : bins)
     if (x.n > 0) live.push_back(&x);
   if (live.empty()) return RVE_OK;
-  if (live.size() == 1) return launch_bin(a, *live[0], s);
+  if (live.size() == 1) return run_one(b, *live[0], a, s);
   RVE_CUDA_TRY(cudaEventRecord(b->ev_fork, s));
   const int ns = std::min<int>(N_SIDE_STREAMS, int(live.size()));
   for (int k = 0; k < ns; ++k) RVE_CUDA_TRY(cudaStreamWaitEvent(b->side[k], b->ev_fork, 0));
-  for (size_t i = 0; i < live.size(); ++i) TRY(launch_bin(a, *live[i], b->side[i % ns]));
+  for (size_t i = 0; i < live.size(); ++i) TRY(run_one(b, *live[i], a, b->side[i % ns]));
   for (int k = 0; k < ns; ++k) {
     RVE_CUDA_TRY(cudaEventRecord(b->ev_join[k], b->side[k]));
     RVE_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_join[k], 0));
@@ -251,8 +321,9 @@ DrArgs<T> make_args(rve_batch* b, const double* F, double tol, int max_iter, dou
   a.sigma = sigma;
   a.iters = iters;
   a.status = status;
-  a.state = static_cast<T*>(state);
+  a.state = static_cast<double*>(state);
   a.valid = P.d_valid;
+  a.last_iters = P.d_last_iters;
   a.warm_start = warm_start;
   a.gP0 = static_cast<T*>(P.d_gP0);
   a.gP1 = static_cast<T*>(P.d_gP1);
@@ -261,6 +332,7 @@ DrArgs<T> make_args(rve_batch* b, const double* F, double tol, int max_iter, dou
   a.max_iter = max_iter;
   a.check_every = b->opt.check_every;
   a.damping = b->opt.damping;
+  a.sigma_tol = b->opt.sigma_tol;
   return a;
 }
 
@@ -288,8 +360,7 @@ int solve_all(rve_batch* b, const double* F, double tol, int max_iter, double* s
   return RVE_OK;
 }
 
-template <typename T>
-__global__ void tan_copy_state(const T* __restrict__ st, T* __restrict__ tan, int64_t total_nf) {
+__global__ void tan_copy_state(const double* __restrict__ st, double* __restrict__ tan, int64_t total_nf) {
   const int64_t n4 = 4 * total_nf;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < int64_t(N_DIRS) * n4;
        i += int64_t(gridDim.x) * blockDim.x)
@@ -334,7 +405,8 @@ int tangent_batched(rve_batch* b, const double* F, double h, double tol, int max
     TRY(dalloc(b, reinterpret_cast<void**>(&b->d_tanI), sizeof(int32_t) * (N_DIRS + 1) * size_t(n)));
     TRY(dalloc(b, reinterpret_cast<void**>(&b->d_tanSt), sizeof(int32_t) * (N_DIRS + 1) * size_t(n)));
   }
-  if (!P.d_tan_state) TRY(dalloc(b, &P.d_tan_state, sizeof(T) * 4 * N_DIRS * size_t(std::max<int64_t>(b->total_nf, 1))));
+  if (!P.d_tan_state)
+    TRY(dalloc(b, &P.d_tan_state, sizeof(double) * 4 * N_DIRS * size_t(std::max<int64_t>(b->total_nf, 1))));
   int32_t* st_base = status ? status : b->d_tanSt + N_DIRS * n;
   int32_t* it_base = b->d_tanI + N_DIRS * n;
   // base solve
@@ -342,7 +414,8 @@ int tangent_batched(rve_batch* b, const double* F, double h, double tol, int max
   TRY(run_bins(b, P.bins, a0, s));
   // perturbed solves, warm-started from the base fluctuation
   if (b->total_nf > 0) {
-    tan_copy_state<T><<<1024, 256, 0, s>>>(static_cast<const T*>(P.d_state), static_cast<T*>(P.d_tan_state), b->total_nf);
+    tan_copy_state<<<1024, 256, 0, s>>>(static_cast<const double*>(P.d_state), static_cast<double*>(P.d_tan_state),
+                                        b->total_nf);
     RVE_CUDA_TRY(cudaGetLastError());
   }
   if (n > 0) {
@@ -354,7 +427,7 @@ int tangent_batched(rve_batch* b, const double* F, double h, double tol, int max
   int64_t scr = 0;
   for (const Bin& bin : P.tan_bins)
     if (bin.mode != 0)
-      for (const Work& w : bin.work) scr += b->topo.meta[w.rve].na;
+      for (const Work& w : bin.work) scr += b->topo.meta[w.rve].na + 1;
   if (scr > 0) {
     if (!P.d_tan_g[0])
       for (int k = 0; k < 3; ++k) TRY(dalloc(b, &P.d_tan_g[k], sizeof(T) * 4 * size_t(scr)));
@@ -380,7 +453,8 @@ extern "C" {
 void rve_options_default(rve_options* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
-  o->tol = 1e-6;
+  o->tol = 3e-7;
+  o->sigma_tol = 0.0;
   o->max_iter = 200000;
   o->check_every = 50;
   o->precision = RVE_PREC_MIXED;
@@ -536,8 +610,11 @@ int rve_solve_subset(rve_batch* b, const int64_t* ids, int64_t m, const double* 
   }
   if (size_t(m) > P.sub_cap) {
     void* p = nullptr;
+    void* q = nullptr;
     TRY(dalloc(b, &p, std::max<size_t>(size_t(m), 1024) * sizeof(Work)));
+    TRY(dalloc(b, &q, std::max<size_t>(size_t(m), 1024) * sizeof(Work)));
     P.d_sub_work = static_cast<Work*>(p);
+    P.d_sub_sorted = static_cast<Work*>(q);
     P.sub_cap = std::max<size_t>(size_t(m), 1024);
   }
   RVE_CUDA_TRY(cudaEventSynchronize(b->ev_work));
@@ -545,6 +622,7 @@ int rve_solve_subset(rve_batch* b, const int64_t* ids, int64_t m, const double* 
   for (Bin& x : bins) {
     std::copy(x.work.begin(), x.work.end(), b->h_work_pin + off);
     x.d_work = P.d_sub_work + off;
+    x.d_sorted = P.d_sub_sorted + off;
     x.n = int(x.work.size());
     off += x.work.size();
   }
@@ -668,15 +746,8 @@ int rve_get_positions(rve_batch* b, int64_t r, const double* F, int32_t precisio
   RVE_CUDA_TRY(cudaMemcpy(&valid, P.d_valid + r, 1, cudaMemcpyDeviceToHost));
   if (!valid) return RVE_OK;
   std::vector<double> h(4 * size_t(M.nf));
-  if (f32) {
-    std::vector<float> hf(4 * size_t(M.nf));
-    RVE_CUDA_TRY(cudaMemcpy(hf.data(), static_cast<float*>(P.d_state) + 4 * size_t(M.node_off),
-                            hf.size() * sizeof(float), cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < hf.size(); ++i) h[i] = hf[i];
-  } else {
-    RVE_CUDA_TRY(cudaMemcpy(h.data(), static_cast<double*>(P.d_state) + 4 * size_t(M.node_off),
-                            h.size() * sizeof(double), cudaMemcpyDeviceToHost));
-  }
+  RVE_CUDA_TRY(cudaMemcpy(h.data(), static_cast<double*>(P.d_state) + 4 * size_t(M.node_off),
+                          h.size() * sizeof(double), cudaMemcpyDeviceToHost));
   for (int a = 0; a < M.nf; ++a) {
     const int i = b->topo.free_node_id[M.node_off + a];
     for (int k = 0; k < 3; ++k) x_out[3 * i + k] += h[4 * a + k];

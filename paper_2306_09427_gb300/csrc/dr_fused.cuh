@@ -14,10 +14,12 @@
 //              s = N / l,  sbar = max(dN/dl, |N|/l)
 //            and stores (s d, sbar) in the fiber scratch SCR;
 //     gather each free node sums +-(s d) and sbar of its incident fibers in
-//            a fixed CSR order (deterministic, no atomics; the paper's
+//            a fixed CSR order, four entries per 8-byte load (runs padded
+//            with a zero slot); deterministic, no atomics (the paper's
 //            getInternalForces scatters with atomics, Sec. 4.3);
 //     check  every check_every iterations: ||f_free||_2 in FP64 against
-//            max(tol R_aff, 1e-16 sum EA); damping re-estimated;
+//            max(tol R_aff, 1e-16 sum EA) and, with sigma_tol > 0, the
+//            estimated remaining stress error; damping re-estimated;
 //     update m = MASS_COEF sbar_sum, v <- ((2-c) v + 2 f/m)/(2+c),
 //            |v| capped, h <- h + v (dt = 1).
 //   finish   sigma = (sigma_bb + sum_e s_e d_e (x) d_e) / (det F V0) with
@@ -31,6 +33,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "rve_internal.h"
 
@@ -156,42 +160,134 @@ __device__ __forceinline__ double law_f64(double eps, double EA, double B) {
   return B > 0.0 ? (EA / B) * expm1(B * eps) : EA * eps;
 }
 
+// Accumulate a fiber's stress terms s d (x) d (o = s d) into FP64 partials
+// (xx yy zz yz xz xy), used by the stress-convergence test at checks.
+template <typename T, typename V4>
+__device__ __forceinline__ void add_virial(double (&ps)[6], const V4& o, T Dx, T Dy, T Dz) {
+  ps[0] += double(o.x * Dx);
+  ps[1] += double(o.y * Dy);
+  ps[2] += double(o.z * Dz);
+  ps[3] += double(o.y * Dz);
+  ps[4] += double(o.x * Dz);
+  ps[5] += double(o.x * Dy);
+}
+
+// Rebase (mixed-precision iterative refinement of the reference state).
+// The FP64 reference fluctuation h_ref of every free node lives in the
+// state slot; the FP32 loop works on the correction d = h - h_ref.  A
+// rebase folds d into h_ref, then recomputes each active fiber's chord
+// g_e = F dX_e + h_ref,j - h_ref,i and Green strain a_e in FP64 and rounds
+// them to the loop type.  Near equilibrium the relaxed strain is small, so
+// its FP32 rounding is tiny in absolute terms, and the correction u is
+// small, so u.(2g + u) keeps full relative precision: the force residual
+// no longer floors at the rounding of |h| ~ one grid spacing.
+// Node part (owned nodes), then a barrier, then the fiber part, then a
+// barrier.  HR is an FP64 scratch copy of h_ref ((nf+1) x 3 doubles).
+template <typename T, int NT, int NPT, typename V4>
+__device__ __forceinline__ void rebase(const DrArgs<T>& A, const Work& wk, const RveMeta& M, const double* sF,
+                                       V4* H, V4* P0, const V4* P1, double* HR, bool init, bool warm,
+                                       T (&hx)[NPT], T (&hy)[NPT], T (&hz)[NPT]) {
+  const int tid = threadIdx.x;
+  const int nf = M.nf, na = M.na;
+  double* st = A.state + 4 * size_t(wk.state_off);
+#pragma unroll
+  for (int q = 0; q < NPT; ++q) {
+    const int a = tid + q * NT;
+    if (a < nf) {
+      double rx = 0.0, ry = 0.0, rz = 0.0;
+      if (!init || warm) {
+        rx = st[4 * a + 0];
+        ry = st[4 * a + 1];
+        rz = st[4 * a + 2];
+      }
+      if (!init) {
+        rx += double(hx[q]);
+        ry += double(hy[q]);
+        rz += double(hz[q]);
+      }
+      st[4 * a + 0] = rx;
+      st[4 * a + 1] = ry;
+      st[4 * a + 2] = rz;
+      st[4 * a + 3] = 0.0;
+      HR[3 * a + 0] = rx;
+      HR[3 * a + 1] = ry;
+      HR[3 * a + 2] = rz;
+      hx[q] = hy[q] = hz[q] = T(0);
+      V4 z;
+      z.x = z.y = z.z = z.w = T(0);
+      H[a] = z;
+    }
+  }
+  if (tid == 0) {
+    HR[3 * nf + 0] = HR[3 * nf + 1] = HR[3 * nf + 2] = 0.0;
+    V4 z;
+    z.x = z.y = z.z = z.w = T(0);
+    H[nf] = z;
+  }
+  __syncthreads();
+  for (int e = tid; e < na; e += NT) {
+    const FibD q = A.fa[M.fa_off + e];
+    const uint32_t ij = k_unpack_ij(P1[e].w);
+    const uint32_t i = ij & 0xffffu, j = ij >> 16;
+    const double gx = sF[0] * q.dx + sF[1] * q.dy + sF[2] * q.dz + (HR[3 * j + 0] - HR[3 * i + 0]);
+    const double gy = sF[3] * q.dx + sF[4] * q.dy + sF[5] * q.dz + (HR[3 * j + 1] - HR[3 * i + 1]);
+    const double gz = sF[6] * q.dx + sF[7] * q.dy + sF[8] * q.dz + (HR[3 * j + 2] - HR[3 * i + 2]);
+    const double L02 = q.L0 * q.L0;
+    V4 p0;
+    p0.x = T(gx);
+    p0.y = T(gy);
+    p0.z = T(gz);
+    p0.w = T(0.5 * (gx * gx + gy * gy + gz * gz - L02) / L02);
+    P0[e] = p0;
+  }
+  __syncthreads();
+}
+
 template <typename T, int NT, int NPT, int MODE>
 __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const DrArgs<T> A) {
   using V4 = typename Vec4<T>::t;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double sF[9], sE[9];
   __shared__ double sRes[8], sBB[12];
+  // loop-carried block-uniform scalars kept in shared memory, not registers
+  // (thresholds; previous stress and residual, double-buffered by check parity)
+  __shared__ double sThr[2], sSig[SIG_WINDOW + 1][8];
 
   const Work wk = A.work[blockIdx.x];
   const RveMeta M = A.meta[wk.rve];
   const int tid = threadIdx.x;
   const int nf = M.nf, na = M.na, nb = M.nb;
 
-  // ---- shared-memory carve-up
+  // ---- shared-memory carve-up (layout mirrored by smem_resident/smem_streamed)
   size_t off = 0;
   auto carve = [&](size_t bytes) {
     unsigned char* p = smem + off;
     off += align_up(bytes, 16);
     return p;
   };
+  const size_t scr_bytes = scr_region_bytes<T>(nf, na);
   V4* H = reinterpret_cast<V4*>(carve(size_t(nf + 1) * sizeof(V4)));
   V4* P0;
   V4* P1;
   V4* SCR;
+  double* HR;
   const uint16_t* CSR;
   if constexpr (MODE == 0) {
     P0 = reinterpret_cast<V4*>(carve(size_t(na) * sizeof(V4)));
     P1 = reinterpret_cast<V4*>(carve(size_t(na) * sizeof(V4)));
-    SCR = reinterpret_cast<V4*>(carve(size_t(na) * sizeof(V4)));
-    CSR = reinterpret_cast<const uint16_t*>(carve(size_t(2 * na) * sizeof(uint16_t)));
+    SCR = reinterpret_cast<V4*>(carve(scr_bytes));
+    HR = reinterpret_cast<double*>(SCR);
+    CSR = reinterpret_cast<const uint16_t*>(carve(size_t(M.csr_len) * sizeof(uint16_t)));
   } else {
     P0 = reinterpret_cast<V4*>(A.gP0) + wk.scr_off;
     P1 = reinterpret_cast<V4*>(A.gP1) + wk.scr_off;
-    if constexpr (MODE == 1)
-      SCR = reinterpret_cast<V4*>(carve(size_t(na) * sizeof(V4)));
-    else
+    if constexpr (MODE == 1) {
+      SCR = reinterpret_cast<V4*>(carve(scr_bytes));
+      HR = reinterpret_cast<double*>(SCR);
+    } else {
       SCR = reinterpret_cast<V4*>(A.gSCR) + wk.scr_off;
+      HR = reinterpret_cast<double*>(carve(size_t(nf + 1) * 3 * sizeof(double)));
+    }
     CSR = A.csr + M.csr_off;
   }
   double* red = reinterpret_cast<double*>(carve(size_t(NT / 32) * 12 * sizeof(double) + 256));
@@ -207,13 +303,10 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
                       sF[2] * (sF[3] * sF[7] - sF[4] * sF[6]);
   const bool badF = !(detF > 0.0) || !(detF < 1e300);  // inverted, degenerate or non-finite F
 
-  // ---- set-up: affine terms of active fibers (FP64), loop parameters
+  // ---- set-up: static loop parameters and the affine force scale (FP64)
   double raff2 = 0.0;
   for (int e = tid; e < na; e += NT) {
     const FibD q = A.fa[M.fa_off + e];
-    const double gx = sF[0] * q.dx + sF[1] * q.dy + sF[2] * q.dz;
-    const double gy = sF[3] * q.dx + sF[4] * q.dy + sF[5] * q.dz;
-    const double gz = sF[6] * q.dx + sF[7] * q.dy + sF[8] * q.dz;
     const double ex = sE[0] * q.dx + sE[1] * q.dy + sE[2] * q.dz;
     const double ey = sE[3] * q.dx + sE[4] * q.dy + sE[5] * q.dz;
     const double ez = sE[6] * q.dx + sE[7] * q.dy + sE[8] * q.dz;
@@ -221,16 +314,11 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
     const double a = (q.dx * ex + q.dy * ey + q.dz * ez + 0.5 * (q.dx * q.dx + q.dy * q.dy + q.dz * q.dz - L02)) / L02;
     const double Na = law_f64(a, q.EA, q.B);
     raff2 += Na * Na;
-    V4 p0, p1;
-    p0.x = T(gx);
-    p0.y = T(gy);
-    p0.z = T(gz);
-    p0.w = T(a);
+    V4 p1;
     p1.x = T(0.5 / L02);
     p1.y = T(q.B > 0.0 ? q.EA / q.B : q.EA);
     p1.z = T(q.B);
     p1.w = k_pack_ij(A.fij[M.fa_off + e], T(0));
-    P0[e] = p0;
     P1[e] = p1;
   }
   // boundary-to-boundary fibers: fixed length, stress share summed once
@@ -256,11 +344,17 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
     sb6[5].add(s * gx * gy);
   }
   if constexpr (MODE == 0) {
-    uint16_t* csr_s = const_cast<uint16_t*>(CSR);
-    const uint16_t* csr_g = A.csr + M.csr_off;
-    for (int k = tid; k < 2 * na; k += NT) csr_s[k] = csr_g[k];
+    // runs are padded to 4 entries and start 8-byte aligned: copy 4 at a time
+    uint2* csr_s = reinterpret_cast<uint2*>(const_cast<uint16_t*>(CSR));
+    const uint2* csr_g = reinterpret_cast<const uint2*>(A.csr + M.csr_off);
+    for (int k = tid; k < M.csr_len / 4; k += NT) csr_s[k] = csr_g[k];
   }
-  // owned free nodes
+  if (tid == 0) {  // zero slot that padded CSR entries point at
+    V4 z;
+    z.x = z.y = z.z = z.w = T(0);
+    SCR[na] = z;
+  }
+  // owned free nodes: correction d (= h - h_ref), velocity, step cap, CSR range
   const bool warm = wk.kind == 1 || (A.warm_start && A.valid[wk.rve]);
   T hx[NPT], hy[NPT], hz[NPT], vx[NPT], vy[NPT], vz[NPT];
   float cap[NPT];
@@ -273,26 +367,9 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
     cap[q] = 0.f;
     cs[q] = 0u;
     if (a < nf) {
-      if (warm) {
-        const V4 s4 = reinterpret_cast<const V4*>(A.state)[size_t(wk.state_off) + a];
-        hx[q] = s4.x;
-        hy[q] = s4.y;
-        hz[q] = s4.z;
-      }
       cap[q] = A.ncap[M.node_off + a];
       cs[q] = A.ncsr[M.node_off + a];
-      V4 h4;
-      h4.x = hx[q];
-      h4.y = hy[q];
-      h4.z = hz[q];
-      h4.w = T(0);
-      H[a] = h4;
     }
-  }
-  if (tid == 0) {
-    V4 z;
-    z.x = z.y = z.z = z.w = T(0);
-    H[nf] = z;
   }
   // boundary-fiber stress share (compensated) -> sBB, then R_aff
   {
@@ -327,7 +404,9 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
   }
   const double thr = fmax(A.tol * sqrt(raff2), ABS_FLOOR * M.sum_EA);
   const double thr2 = thr * thr;
-  __syncthreads();  // red reuse and set-up writes visible
+  // initial reference state: h_ref = warm state or 0 (P1 and CSR written above)
+  __syncthreads();
+  rebase<T, NT, NPT>(A, wk, M, sF, H, P0, P1, HR, true, warm, hx, hy, hz);
 
   // ---- dynamic relaxation loop
   const int K = A.check_every;
@@ -336,26 +415,50 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
   T alpha = T((2.0 - c) / (2.0 + c)), beta = T(2.0 / (2.0 + c));
   double pre = 0.0, pm = 0.0;  // thread partials from the iteration before a check
   bool have_pre = false;
-  int it = 0;
+  int it = 0, n_checks = 0;
+  // stress-convergence test: below thr_tight the residual alone decides
+  const bool sig_test = A.sigma_tol > 0.0;
+  if (tid == 0) {
+    const double thr_tight = fmax(1e-3 * A.sigma_tol * sqrt(raff2), ABS_FLOOR * M.sum_EA);
+    sThr[0] = thr2;
+    sThr[1] = thr_tight * thr_tight;
+    for (int k = 0; k <= SIG_WINDOW; ++k) sSig[k][7] = 0.0;  // "record present" flags
+  }
+  __syncthreads();
   int status = RVE_STATUS_EMPTY;
   if (nf > 0 && !badF) {
     status = RVE_STATUS_MAX_ITER;
     for (;; ++it) {
-      // fiber phase
-      for (int e = tid; e < na; e += NT) {
-        const V4 p0 = P0[e];
-        const V4 p1 = P1[e];
-        const uint32_t ij = k_unpack_ij(p1.w);
-        const V4 hi = H[ij & 0xffffu];
-        const V4 hj = H[ij >> 16];
+      const bool check = (it % K == 0) || (it >= A.max_iter);
+      const bool want_sig = check && sig_test;
+      double ps[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      // fiber phase (two fibers per step: independent shared-memory loads overlap)
+      for (int e = tid; e < na; e += 2 * NT) {
+        const int e2 = e + NT;
+        const bool two = e2 < na;
+        const V4 p0a = P0[e], p1a = P1[e];
+        const V4 p0b = P0[two ? e2 : e], p1b = P1[two ? e2 : e];
+        const uint32_t ija = k_unpack_ij(p1a.w), ijb = k_unpack_ij(p1b.w);
+        const V4 hia = H[ija & 0xffffu], hja = H[ija >> 16];
+        const V4 hib = H[ijb & 0xffffu], hjb = H[ijb >> 16];
         T Dx, Dy, Dz, s, sbar;
-        fiber_force<T>(p0, p1, hi, hj, Dx, Dy, Dz, s, sbar);
+        fiber_force<T>(p0a, p1a, hia, hja, Dx, Dy, Dz, s, sbar);
         V4 o;
         o.x = s * Dx;
         o.y = s * Dy;
         o.z = s * Dz;
         o.w = sbar;
         SCR[e] = o;
+        if (want_sig) add_virial(ps, o, Dx, Dy, Dz);
+        if (two) {
+          fiber_force<T>(p0b, p1b, hib, hjb, Dx, Dy, Dz, s, sbar);
+          o.x = s * Dx;
+          o.y = s * Dy;
+          o.z = s * Dz;
+          o.w = sbar;
+          SCR[e2] = o;
+          if (want_sig) add_virial(ps, o, Dx, Dy, Dz);
+        }
       }
       __syncthreads();
       // gather
@@ -365,26 +468,23 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
         fx[q] = fy[q] = fz[q] = fw[q] = T(0);
         const int a = tid + q * NT;
         if (a < nf) {
-          const uint32_t b = cs[q] >> 8, n = cs[q] & 0xffu;
-          for (uint32_t k = 0; k < n; ++k) {
-            const uint32_t ent = CSR[b + k];
-            const V4 s4 = SCR[ent >> 1];
-            if (ent & 1u) {
-              fx[q] -= s4.x;
-              fy[q] -= s4.y;
-              fz[q] -= s4.z;
-            } else {
-              fx[q] += s4.x;
-              fy[q] += s4.y;
-              fz[q] += s4.z;
-            }
-            fw[q] += s4.w;
+          const uint32_t b = cs[q] >> 8, n = cs[q] & 0xffu;  // n is a multiple of 4
+          for (uint32_t k = 0; k < n; k += 4) {
+            const uint2 pk = *reinterpret_cast<const uint2*>(CSR + b + k);
+            const uint32_t e0 = pk.x & 0xffffu, e1 = pk.x >> 16, e2 = pk.y & 0xffffu, e3 = pk.y >> 16;
+            const V4 s0 = SCR[e0 >> 1], s1 = SCR[e1 >> 1], s2 = SCR[e2 >> 1], s3 = SCR[e3 >> 1];
+            const T g0 = (e0 & 1u) ? T(-1) : T(1), g1 = (e1 & 1u) ? T(-1) : T(1);
+            const T g2 = (e2 & 1u) ? T(-1) : T(1), g3 = (e3 & 1u) ? T(-1) : T(1);
+            fx[q] += g0 * s0.x + g1 * s1.x + g2 * s2.x + g3 * s3.x;
+            fy[q] += g0 * s0.y + g1 * s1.y + g2 * s2.y + g3 * s3.y;
+            fz[q] += g0 * s0.z + g1 * s1.z + g2 * s2.z + g3 * s3.z;
+            fw[q] += (s0.w + s1.w) + (s2.w + s3.w);
           }
         }
       }
-      const bool check = (it % K == 0) || (it >= A.max_iter);
+      bool do_rebase = false;
       if (check) {
-        double v3[3] = {0.0, 0.0, 0.0};
+        double v3[9] = {0.0, 0.0, 0.0, ps[0], ps[1], ps[2], ps[3], ps[4], ps[5]};
 #pragma unroll
         for (int q = 0; q < NPT; ++q) {
           if (tid + q * NT < nf) {
@@ -394,12 +494,40 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
         }
         v3[1] -= pre;
         v3[2] = pm;
-        block_allreduce<NT, 3>(v3, red);
+        block_allreduce<NT, 9>(v3, red);  // also: every gather of SCR is done
         if (!(v3[0] < 1e300)) {  // NaN or Inf
           status = RVE_STATUS_NONFINITE;
           break;
         }
-        if (v3[0] <= thr2) {
+        bool sig_ok = true;
+        if (sig_test && v3[0] > sThr[1]) {
+          // remaining stress error of a geometrically converging sequence, from
+          // the stress and residual SIG_WINDOW checks back (ring of records)
+          const double* prev = sSig[(n_checks + 1) % (SIG_WINDOW + 1)];
+          double* next = sSig[n_checks % (SIG_WINDOW + 1)];
+          const double r = sqrt(v3[0]);
+          double dn = 0.0, nn = 0.0;
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            const double sg = v3[3 + k] + sBB[2 * k] + sBB[2 * k + 1];
+            const double wk2 = k < 3 ? 1.0 : 2.0;  // off-diagonal entries appear twice
+            dn += wk2 * (sg - prev[k]) * (sg - prev[k]);
+            nn += wk2 * sg * sg;
+            if (tid == 0) next[k] = sg;
+          }
+          sig_ok = false;
+          if (prev[7] != 0.0 && nn > 0.0) {
+            const double rho = fmin(r / prev[6], SIG_RHO_CAP);
+            sig_ok = sqrt(dn / nn) * rho / (1.0 - rho) <= A.sigma_tol;
+          }
+          if (tid == 0) {
+            next[6] = r;
+            next[7] = 1.0;
+          }
+        } else if (sig_test && tid == 0) {
+          sSig[n_checks % (SIG_WINDOW + 1)][7] = 0.0;
+        }
+        if (v3[0] <= sThr[0] && sig_ok) {
           status = RVE_STATUS_CONVERGED;
           break;
         }
@@ -415,6 +543,8 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
         pre = 0.0;
         pm = 0.0;
         have_pre = false;
+        ++n_checks;
+        do_rebase = std::is_same<T, float>::value && (n_checks % REBASE_EVERY == 0);
       }
       const bool pre_it = adaptive && ((it + 1) % K == 0);
       // update owned nodes
@@ -454,11 +584,15 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
         }
       }
       if (pre_it) have_pre = true;
-      __syncthreads();
+      if (do_rebase) {
+        rebase<T, NT, NPT>(A, wk, M, sF, H, P0, P1, HR, false, true, hx, hy, hz);
+      } else {
+        __syncthreads();
+      }
     }
   }
 
-  // ---- stress: active fibers at the final state (H holds it)
+  // ---- stress: active fibers at the final state (P0 at h_ref, H holds d)
   CSum s6[6];
   for (int e = tid; e < na; e += NT) {
     const V4 p0 = P0[e];
@@ -498,31 +632,34 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
     }
     sRes[tid] = s + cc;
   }
-  // save state
+  // save state: h = h_ref + d (FP64)
+  {
+    double* st = A.state + 4 * size_t(wk.state_off);
 #pragma unroll
-  for (int q = 0; q < NPT; ++q) {
-    const int a = tid + q * NT;
-    if (a < nf) {
-      V4 h4;
-      h4.x = hx[q];
-      h4.y = hy[q];
-      h4.z = hz[q];
-      h4.w = T(0);
-      reinterpret_cast<V4*>(A.state)[size_t(wk.state_off) + a] = h4;
+    for (int q = 0; q < NPT; ++q) {
+      const int a = tid + q * NT;
+      if (a < nf) {
+        st[4 * a + 0] += double(hx[q]);
+        st[4 * a + 1] += double(hy[q]);
+        st[4 * a + 2] += double(hz[q]);
+      }
     }
   }
   __syncthreads();
   if (tid < 9) {
     // sigma components in order xx yy zz yz xz xy
     const int i = tid / 3, j = tid % 3;
-    const int map[9] = {0, 5, 4, 5, 1, 3, 4, 3, 2};
+    const int idx = (i == j) ? i : 6 - i - j;
     A.sigma[9 * size_t(wk.out) + tid] = badF ? __longlong_as_double(0x7ff8000000000000ll)
-                                              : sRes[map[3 * i + j]] / (detF * M.V0);
+                                              : sRes[idx] / (detF * M.V0);
   }
   if (tid == 0) {
     int st = status;
     if (badF) st = RVE_STATUS_NONFINITE;
-    if (wk.kind == 0) A.valid[wk.rve] = (st == RVE_STATUS_NONFINITE) ? 0 : 1;  // never warm-start from NaN
+    if (wk.kind == 0) {
+      A.valid[wk.rve] = (st == RVE_STATUS_NONFINITE) ? 0 : 1;  // never warm-start from NaN
+      A.last_iters[wk.rve] = it;
+    }
     if (A.iters) A.iters[wk.out] = it;
     if (A.status) A.status[wk.out] = st;
   }

@@ -91,7 +91,10 @@ __global__ void pl_setup(const RveMeta* meta, int r, const FibD* fa, const uint3
     B.H[a] = h;
     B.V[a] = dvec4{0.0, 0.0, 0.0, 0.0};
   }
-  if (tid == 0) B.H[M.nf] = dvec4{0.0, 0.0, 0.0, 0.0};
+  if (tid == 0) {
+    B.H[M.nf] = dvec4{0.0, 0.0, 0.0, 0.0};
+    B.SCR[M.na] = dvec4{0.0, 0.0, 0.0, 0.0};  // zero slot of the padded CSR runs
+  }
   const int warp = tid >> 5, lane = tid & 31;
   const double r2 = warp_sum(raff2);
   for (int k = 0; k < 6; ++k) {
@@ -124,15 +127,38 @@ __global__ void pl_setup(const RveMeta* meta, int r, const FibD* fa, const uint3
   }
 }
 
-__global__ void pl_fiber(int na, PlainBufs B) {
+// per active fiber: (s d, sbar); with want_sig also per-block stress partials
+__global__ void pl_fiber(int na, int want_sig, PlainBufs B) {
   const int e = blockIdx.x * PT + threadIdx.x;
-  if (e >= na) return;
-  const dvec4 p0 = B.P0[e], p1 = B.P1[e];
-  const uint32_t ij = static_cast<uint32_t>(p1.w);
-  const dvec4 hi = B.H[ij & 0xffffu], hj = B.H[ij >> 16];
-  double Dx, Dy, Dz, s, sbar;
-  fiber_force<double>(p0, p1, hi, hj, Dx, Dy, Dz, s, sbar);
-  B.SCR[e] = dvec4{s * Dx, s * Dy, s * Dz, sbar};
+  double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (e < na) {
+    const dvec4 p0 = B.P0[e], p1 = B.P1[e];
+    const uint32_t ij = static_cast<uint32_t>(p1.w);
+    const dvec4 hi = B.H[ij & 0xffffu], hj = B.H[ij >> 16];
+    double Dx, Dy, Dz, s, sbar;
+    fiber_force<double>(p0, p1, hi, hj, Dx, Dy, Dz, s, sbar);
+    const dvec4 o{s * Dx, s * Dy, s * Dz, sbar};
+    B.SCR[e] = o;
+    t[0] = o.x * Dx;
+    t[1] = o.y * Dy;
+    t[2] = o.z * Dz;
+    t[3] = o.y * Dz;
+    t[4] = o.x * Dz;
+    t[5] = o.x * Dy;
+  }
+  if (!want_sig) return;
+  __shared__ double red[6 * (PT / 32)];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = 0; k < 6; ++k) {
+    const double v = warp_sum(t[k]);
+    if (lane == 0) red[6 * warp + k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double v = 0.0;
+    for (int w = 0; w < PT / 32; ++w) v += red[6 * w + threadIdx.x];
+    B.sig[12 * blockIdx.x + threadIdx.x] = v;
+  }
 }
 
 __device__ __forceinline__ void pl_gather(int a, const RveMeta& M, const uint16_t* csr, const uint32_t* ncsr,
@@ -242,20 +268,24 @@ __global__ void pl_node_apply(const RveMeta* meta, int r, const float* ncap, dou
   if (pre_it) block_pair(pre, pm, B.part, 0);
 }
 
-__global__ void pl_reduce(int nblk, PlainBufs B) {
-  __shared__ double red[4 * (PT / 32)];
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+// res[16..19] = pre, pm, r2, post; res[20..25] = stress partial sums
+__global__ void pl_reduce(int nblk, int nblk_a, int want_sig, PlainBufs B) {
+  __shared__ double red[10 * (PT / 32)];
+  double v[10] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int b = threadIdx.x; b < nblk; b += PT)
     for (int k = 0; k < 4; ++k) v[k] += B.part[4 * b + k];
+  if (want_sig)
+    for (int b = threadIdx.x; b < nblk_a; b += PT)
+      for (int k = 0; k < 6; ++k) v[4 + k] += B.sig[12 * b + k];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 10; ++k) {
     v[k] = warp_sum(v[k]);
-    if (lane == 0) red[4 * warp + k] = v[k];
+    if (lane == 0) red[10 * warp + k] = v[k];
   }
   __syncthreads();
-  if (threadIdx.x < 4) {
+  if (threadIdx.x < 10) {
     double s = 0.0;
-    for (int w = 0; w < PT / 32; ++w) s += red[4 * w + threadIdx.x];
+    for (int w = 0; w < PT / 32; ++w) s += red[10 * w + threadIdx.x];
     B.res[16 + threadIdx.x] = s;
   }
 }
@@ -341,22 +371,20 @@ __global__ void pl_save(const RveMeta* meta, int r, double* state, PlainBufs B) 
 
 int plain_scratch_bytes(int nf_max, int na_max) {
   const int nblk_n = (nf_max + PT - 1) / PT + 1, nblk_a = (na_max + PT - 1) / PT + 1;
-  return int(sizeof(dvec4)) * (3 * na_max + 3 * (nf_max + 1)) + 8 * (4 * nblk_n + 32 + 12 * nblk_a) + 1024;
+  return int(sizeof(dvec4)) * (3 * (na_max + 1) + 3 * (nf_max + 1)) + 8 * (4 * nblk_n + 32 + 12 * nblk_a) + 1024;
 }
 
-// Solve RVE `r` with F[9*out..] on `s`, outputs at index `out`.
-int plain_solve_one(rve_batch* b, int r, int out, const double* F, double tol, int max_iter, double* sigma,
-                    int32_t* iters, int32_t* status, cudaStream_t s) {
-  const RveMeta& M = b->topo.meta[r];
-  unsigned char* base = reinterpret_cast<unsigned char*>(b->d_pl);
+namespace {
+
+// Carve the plain path's working buffers for one RVE out of `base`;
+// returns the bytes used (256-byte aligned pieces).
+size_t carve_plain(unsigned char* base, int nf, int na, PlainBufs& B) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
     unsigned char* p = base + off;
     off += align_up(bytes, 256);
     return p;
   };
-  const int na = M.na, nf = M.nf;
-  PlainBufs B;
   B.P0 = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(na + 1)));
   B.P1 = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(na + 1)));
   B.SCR = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(na + 1)));
@@ -367,44 +395,83 @@ int plain_solve_one(rve_batch* b, int r, int out, const double* F, double tol, i
   B.part = reinterpret_cast<double*>(take(sizeof(double) * 4 * size_t(nblk_n + 1)));
   B.res = reinterpret_cast<double*>(take(sizeof(double) * 32));
   B.sig = reinterpret_cast<double*>(take(sizeof(double) * 12 * size_t(nblk_a + 1)));
-  if (off > b->pl_bytes) return fail(RVE_EINVAL, "plain scratch too small");
-  RVE_CUDA_TRY(cudaMemsetAsync(B.part, 0, sizeof(double) * 4 * size_t(nblk_n + 1), s));
+  return off;
+}
 
-  pl_setup<<<1, PT, 0, s>>>(b->d_meta, r, b->d_fa, b->d_fij, b->d_fb, F, out, static_cast<double*>(b->pd.d_state),
-                            b->pd.d_valid, b->opt.warm_start, B);
+// Set-up and host-driven DR loop of the plain path for RVE r (F[9*out..]).
+// On return it / st hold the iterations and status; B.H holds the final state.
+int plain_run(rve_batch* b, int r, int out, const double* F, double tol, int max_iter, const PlainBufs& B,
+              cudaStream_t s, const double* state, const uint8_t* valid, int warm_start, int& it_out, int& st_out) {
+  const RveMeta& M = b->topo.meta[r];
+  const int na = M.na, nf = M.nf;
+  const int nblk_n = (nf + PT - 1) / PT, nblk_a = (na + PT - 1) / PT;
+  RVE_CUDA_TRY(cudaMemsetAsync(B.part, 0, sizeof(double) * 4 * size_t(nblk_n + 1), s));
+  RVE_CUDA_TRY(cudaMemsetAsync(B.res, 0, sizeof(double) * 32, s));
+  pl_setup<<<1, PT, 0, s>>>(b->d_meta, r, b->d_fa, b->d_fij, b->d_fb, F, out, state, valid, warm_start, B);
   RVE_CUDA_TRY(cudaGetLastError());
   RVE_CUDA_TRY(cudaMemcpyAsync(b->h_pl, B.res, 14 * sizeof(double), cudaMemcpyDeviceToHost, s));
   RVE_CUDA_TRY(cudaStreamSynchronize(s));
+  const double raff = std::sqrt(b->h_pl[0]);
+  double sbb[6];
+  for (int k = 0; k < 6; ++k) sbb[k] = b->h_pl[1 + 2 * k] + b->h_pl[2 + 2 * k];
   const double detF = b->h_pl[13];
-  const bool badF = !(detF > 0.0) || !(detF < 1e300);  // reported as non-finite by pl_finish
-  const double thr = std::fmax(tol * std::sqrt(b->h_pl[0]), ABS_FLOOR * M.sum_EA);
+  const bool badF = !(detF > 0.0) || !(detF < 1e300);  // reported as non-finite by the finish kernel
+  const double thr = std::fmax(tol * raff, ABS_FLOOR * M.sum_EA);
   const double thr2 = thr * thr;
+  const bool sig_test = b->opt.sigma_tol > 0.0;
+  const double thr_tight = std::fmax(1e-3 * b->opt.sigma_tol * raff, ABS_FLOOR * M.sum_EA);
   const int K = b->opt.check_every;
   const bool adaptive = !(b->opt.damping > 0.0);
   double c = adaptive ? DAMP_C0 : b->opt.damping;
   double alpha = (2.0 - c) / (2.0 + c), beta = 2.0 / (2.0 + c);
   bool have_pre = false;
+  double sig_hist[SIG_WINDOW + 1][8] = {};  // ring of (stress, residual, present) per check
+  int n_checks = 0;
   int it = 0, st = RVE_STATUS_EMPTY;
   if (nf > 0 && !badF) {
     st = RVE_STATUS_MAX_ITER;
     for (;; ++it) {
-      pl_fiber<<<(na + PT - 1) / PT, PT, 0, s>>>(na, B);
       const bool check = (it % K == 0) || it >= max_iter;
       const int pre_it = adaptive && ((it + 1) % K == 0);
+      pl_fiber<<<(na + PT - 1) / PT, PT, 0, s>>>(na, check && sig_test, B);
       if (!check) {
         pl_node<<<nblk_n, PT, 0, s>>>(b->d_meta, r, b->d_csr, b->d_ncsr, b->d_ncap, alpha, beta, pre_it, B);
       } else {
         pl_node_check<<<nblk_n, PT, 0, s>>>(b->d_meta, r, b->d_csr, b->d_ncsr, B);
-        pl_reduce<<<1, PT, 0, s>>>(nblk_n, B);
+        pl_reduce<<<1, PT, 0, s>>>(nblk_n, nblk_a, sig_test, B);
         RVE_CUDA_TRY(cudaGetLastError());
-        RVE_CUDA_TRY(cudaMemcpyAsync(b->h_pl, B.res + 16, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        RVE_CUDA_TRY(cudaMemcpyAsync(b->h_pl, B.res + 16, 10 * sizeof(double), cudaMemcpyDeviceToHost, s));
         RVE_CUDA_TRY(cudaStreamSynchronize(s));
         const double pre = b->h_pl[0], pm = b->h_pl[1], r2 = b->h_pl[2], post = b->h_pl[3];
         if (!(r2 < 1e300)) {
           st = RVE_STATUS_NONFINITE;
           break;
         }
-        if (r2 <= thr2) {
+        bool sig_ok = true;
+        double* next = sig_hist[n_checks % (SIG_WINDOW + 1)];
+        if (sig_test && r2 > thr_tight * thr_tight) {
+          const double* prev = sig_hist[(n_checks + 1) % (SIG_WINDOW + 1)];
+          const double rr = std::sqrt(r2);
+          double dn = 0.0, nn = 0.0;
+          for (int k = 0; k < 6; ++k) {
+            const double sg = b->h_pl[4 + k] + sbb[k];
+            const double wk2 = k < 3 ? 1.0 : 2.0;
+            dn += wk2 * (sg - prev[k]) * (sg - prev[k]);
+            nn += wk2 * sg * sg;
+            next[k] = sg;
+          }
+          sig_ok = false;
+          if (prev[7] != 0.0 && nn > 0.0) {
+            const double rho = std::fmin(rr / prev[6], SIG_RHO_CAP);
+            sig_ok = std::sqrt(dn / nn) * rho / (1.0 - rho) <= b->opt.sigma_tol;
+          }
+          next[6] = rr;
+          next[7] = 1.0;
+        } else {
+          next[7] = 0.0;
+        }
+        ++n_checks;
+        if (r2 <= thr2 && sig_ok) {
           st = RVE_STATUS_CONVERGED;
           break;
         }
@@ -423,9 +490,29 @@ int plain_solve_one(rve_batch* b, int r, int out, const double* F, double tol, i
       have_pre = pre_it != 0;
     }
   }
-  if (na > 0) pl_sigma<<<nblk_a, PT, 0, s>>>(na, B);
-  pl_finish<<<1, 32, 0, s>>>(b->d_meta, r, na > 0 ? nblk_a : 0, F, out, it, st, sigma, iters, status, b->pd.d_valid, B);
-  if (nf > 0) pl_save<<<nblk_n, PT, 0, s>>>(b->d_meta, r, static_cast<double*>(b->pd.d_state), B);
+  it_out = it;
+  st_out = st;
+  return RVE_OK;
+}
+
+}  // namespace
+
+// Solve RVE `r` with F[9*out..] on `s`, outputs at index `out`.
+int plain_solve_one(rve_batch* b, int r, int out, const double* F, double tol, int max_iter, double* sigma,
+                    int32_t* iters, int32_t* status, cudaStream_t s) {
+  const RveMeta& M = b->topo.meta[r];
+  PlainBufs B;
+  if (carve_plain(reinterpret_cast<unsigned char*>(b->d_pl), M.nf, M.na, B) > b->pl_bytes)
+    return fail(RVE_EINVAL, "plain scratch too small");
+  int it = 0, st = 0;
+  const int rc = plain_run(b, r, out, F, tol, max_iter, B, s, static_cast<double*>(b->pd.d_state), b->pd.d_valid,
+                           b->opt.warm_start, it, st);
+  if (rc != RVE_OK) return rc;
+  const int nblk_n = (M.nf + PT - 1) / PT, nblk_a = (M.na + PT - 1) / PT;
+  if (M.na > 0) pl_sigma<<<nblk_a, PT, 0, s>>>(M.na, B);
+  pl_finish<<<1, 32, 0, s>>>(b->d_meta, r, M.na > 0 ? nblk_a : 0, F, out, it, st, sigma, iters, status,
+                             b->pd.d_valid, B);
+  if (M.nf > 0) pl_save<<<nblk_n, PT, 0, s>>>(b->d_meta, r, static_cast<double*>(b->pd.d_state), B);
   RVE_CUDA_TRY(cudaGetLastError());
   return RVE_OK;
 }
@@ -523,82 +610,14 @@ extern "C" int rve_solve_plain_noalloc(rve_batch* b, int64_t r, const double* F,
     base_v = g_noalloc_addr[b->device];
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  unsigned char* base = static_cast<unsigned char*>(base_v);
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    unsigned char* p = base + off;
-    off += na_align(bytes);
-    return p;
-  };
-  const int na = M.na, nf = M.nf;
   PlainBufs B;
-  B.P0 = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(na + 1)));
-  B.P1 = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(na + 1)));
-  B.SCR = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(na + 1)));
-  B.H = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(nf + 1)));
-  B.V = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(nf + 1)));
-  B.Fn = reinterpret_cast<dvec4*>(take(sizeof(dvec4) * size_t(nf + 1)));
-  const int nblk_n = (nf + PT - 1) / PT, nblk_a = (na + PT - 1) / PT;
-  B.part = reinterpret_cast<double*>(take(sizeof(double) * 4 * size_t(nblk_n + 1)));
-  B.res = reinterpret_cast<double*>(take(sizeof(double) * 32));
-  B.sig = reinterpret_cast<double*>(take(sizeof(double) * 12 * size_t(nblk_a + 1)));
-  if (off > noalloc_bytes()) return fail(RVE_EINVAL, "internal: no-alloc scratch layout overflow");
-  // the array keeps the previous call's contents: clear what is accumulated
-  RVE_CUDA_TRY(cudaMemsetAsync(B.part, 0, sizeof(double) * 4 * size_t(nblk_n + 1), s));
-  RVE_CUDA_TRY(cudaMemsetAsync(B.res, 0, sizeof(double) * 32, s));
-
-  pl_setup<<<1, PT, 0, s>>>(b->d_meta, int(r), b->d_fa, b->d_fij, b->d_fb, F, 0, nullptr, nullptr, 0, B);
-  RVE_CUDA_TRY(cudaGetLastError());
-  RVE_CUDA_TRY(cudaMemcpyAsync(b->h_pl, B.res, 14 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  RVE_CUDA_TRY(cudaStreamSynchronize(s));
-  const double detF = b->h_pl[13];
-  const bool badF = !(detF > 0.0) || !(detF < 1e300);
-  const double thr = std::fmax(tol * std::sqrt(b->h_pl[0]), ABS_FLOOR * M.sum_EA);
-  const double thr2 = thr * thr;
-  const int K = b->opt.check_every;
-  const bool adaptive = !(b->opt.damping > 0.0);
-  double c = adaptive ? DAMP_C0 : b->opt.damping;
-  double alpha = (2.0 - c) / (2.0 + c), beta = 2.0 / (2.0 + c);
-  bool have_pre = false;
-  int it = 0, st = RVE_STATUS_EMPTY;
-  if (nf > 0 && !badF) {
-    st = RVE_STATUS_MAX_ITER;
-    for (;; ++it) {
-      pl_fiber<<<(na + PT - 1) / PT, PT, 0, s>>>(na, B);
-      const bool check = (it % K == 0) || it >= max_iter;
-      const int pre_it = adaptive && ((it + 1) % K == 0);
-      if (!check) {
-        pl_node<<<nblk_n, PT, 0, s>>>(b->d_meta, int(r), b->d_csr, b->d_ncsr, b->d_ncap, alpha, beta, pre_it, B);
-      } else {
-        pl_node_check<<<nblk_n, PT, 0, s>>>(b->d_meta, int(r), b->d_csr, b->d_ncsr, B);
-        pl_reduce<<<1, PT, 0, s>>>(nblk_n, B);
-        RVE_CUDA_TRY(cudaGetLastError());
-        RVE_CUDA_TRY(cudaMemcpyAsync(b->h_pl, B.res + 16, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        RVE_CUDA_TRY(cudaStreamSynchronize(s));
-        const double pre = b->h_pl[0], pm = b->h_pl[1], r2 = b->h_pl[2], post = b->h_pl[3];
-        if (!(r2 < 1e300)) {
-          st = RVE_STATUS_NONFINITE;
-          break;
-        }
-        if (r2 <= thr2) {
-          st = RVE_STATUS_CONVERGED;
-          break;
-        }
-        if (it >= max_iter) break;
-        if (adaptive && have_pre && pm > 0.0) {
-          const double lam = -(post - pre) / pm;
-          if (lam > 0.0) {
-            c = std::fmin(2.0 * std::sqrt(lam), DAMP_C_MAX);
-            alpha = (2.0 - c) / (2.0 + c);
-            beta = 2.0 / (2.0 + c);
-          }
-        }
-        pl_node_apply<<<nblk_n, PT, 0, s>>>(b->d_meta, int(r), b->d_ncap, alpha, beta, pre_it, B);
-      }
-      RVE_CUDA_TRY(cudaGetLastError());
-      have_pre = pre_it != 0;
-    }
-  }
+  if (carve_plain(static_cast<unsigned char*>(base_v), M.nf, M.na, B) > noalloc_bytes())
+    return fail(RVE_EINVAL, "internal: no-alloc scratch layout overflow");
+  // the array keeps the previous call's contents; plain_run clears what accumulates
+  int it = 0, st = 0;
+  const int rc = plain_run(b, int(r), 0, F, tol, max_iter, B, s, nullptr, nullptr, 0, it, st);
+  if (rc != RVE_OK) return rc;
+  const int na = M.na, nblk_a = (na + PT - 1) / PT;
   if (na > 0) pl_sigma<<<nblk_a, PT, 0, s>>>(na, B);
   pl_finish_noalloc<<<1, 32, 0, s>>>(b->d_meta, int(r), na > 0 ? nblk_a : 0, F, it, st, sigma, iters, status, B);
   RVE_CUDA_TRY(cudaGetLastError());

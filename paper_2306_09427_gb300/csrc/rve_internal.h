@@ -32,7 +32,9 @@ struct RveMeta {
   int32_t node_off; // offset into per-free-node arrays
   int32_t fa_off;   // offset into active-fiber arrays
   int32_t fb_off;   // offset into boundary-fiber arrays
-  int32_t csr_off;  // offset into CSR entries (2*na per RVE)
+  int32_t csr_off;  // offset into CSR entries (a multiple of 4)
+  int32_t csr_len;  // CSR entries of this RVE (each node's run padded to 4)
+  int32_t pad_;
   double V0;        // reference volume
   double sum_EA;    // sum of EA over kept fibers (absolute residual floor)
 };
@@ -66,23 +68,39 @@ constexpr double STEP_CAP = 0.1;
 constexpr double DAMP_C0 = 0.1;
 constexpr double DAMP_C_MAX = 1.9;
 constexpr double ABS_FLOOR = 1e-16;  // absolute residual floor per unit EA
+constexpr int REBASE_EVERY = 4;      // FP32 path: rebase the reference state every 4 checks
+// stress-convergence estimate: stress and residual compared SIG_WINDOW
+// checks apart, contraction ratio capped at SIG_RHO_CAP
+constexpr int SIG_WINDOW = 2;
+constexpr double SIG_RHO_CAP = 0.95;
 
 // Shared-memory footprint of one RVE held by the fused kernel.
-// resident: P0, P1, SCR (one 4-vector each per active fiber), H (nf+1
-// 4-vectors), CSR entries (2*na u16) and a reduction buffer.
-// streamed: H and SCR only when they fit, otherwise H only.
+// resident: P0, P1 (one 4-vector each per active fiber), SCR (na+1
+// 4-vectors: slot na stays zero for CSR padding), H (nf+1 4-vectors), CSR
+// entries (csr_len u16) and a reduction buffer.
+// streamed: H and SCR only when they fit, otherwise H and the FP64
+// reference copy.
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 inline size_t red_bytes(int nt) { return align_up(size_t(nt / 32) * 12 * sizeof(double) + 256, 16); }
+// The fiber-scratch region also holds the FP64 reference state (3 doubles
+// per node) during a rebase, so it is the larger of the two.
 template <typename T>
-inline size_t smem_resident(int nf, int na, int nt) {
+__host__ __device__ inline size_t scr_region_bytes(int nf, int na) {
+  const size_t a = size_t(na + 1) * 4 * sizeof(T), b = size_t(nf + 1) * 3 * sizeof(double);
+  return a > b ? a : b;
+}
+template <typename T>
+inline size_t smem_resident(int nf, int na, int csr_len, int nt) {
   const size_t v4 = 4 * sizeof(T);
-  return 3 * align_up(size_t(na) * v4, 16) + align_up(size_t(nf + 1) * v4, 16) +
-         align_up(size_t(2 * na) * sizeof(uint16_t), 16) + red_bytes(nt);
+  return 2 * align_up(size_t(na) * v4, 16) + align_up(scr_region_bytes<T>(nf, na), 16) +
+         align_up(size_t(nf + 1) * v4, 16) + align_up(size_t(csr_len) * sizeof(uint16_t), 16) + red_bytes(nt);
 }
 template <typename T>
 inline size_t smem_streamed(int nf, int na, int nt, bool scr_in_smem) {
   const size_t v4 = 4 * sizeof(T);
-  return align_up(size_t(nf + 1) * v4, 16) + (scr_in_smem ? align_up(size_t(na) * v4, 16) : 0) +
+  return align_up(size_t(nf + 1) * v4, 16) +
+         (scr_in_smem ? align_up(scr_region_bytes<T>(nf, na), 16)
+                      : align_up(size_t(nf + 1) * 3 * sizeof(double), 16)) +
          red_bytes(nt);
 }
 
@@ -97,7 +115,8 @@ struct DrArgs {
   const FibD* fa;          // active fibers
   const uint32_t* fij;     // packed endpoints i | j << 16 (nf = boundary zero slot)
   const FibD* fb;          // boundary-to-boundary fibers
-  const uint16_t* csr;     // per free node: (active fiber << 1) | (node is endpoint j)
+  const uint16_t* csr;     // per free node: (active fiber << 1) | (node is endpoint j), runs padded to 4
+                           // entries with (na << 1) (the zero scratch slot)
   const uint32_t* ncsr;    // per free node: (local CSR begin << 8) | count
   const float* ncap;       // per free node: STEP_CAP * min incident L0
   const Work* work;
@@ -106,8 +125,9 @@ struct DrArgs {
   double* sigma;           // 9 per output index
   int32_t* iters;          // per output index (may be null)
   int32_t* status;         // per output index (may be null)
-  T* state;                // 4 per state node (x, y, z, unused)
+  double* state;           // 4 per state node: FP64 fluctuation h (x, y, z, unused)
   uint8_t* valid;          // per RVE: own state slot holds a solve
+  int32_t* last_iters;     // per RVE: iterations of its last own-slot solve (scheduling cost)
   int32_t warm_start;
   // streamed bins: per-solve scratch in global memory (Work::scr_off)
   T* gP0;
@@ -117,6 +137,7 @@ struct DrArgs {
   int32_t max_iter;
   int32_t check_every;
   double damping;          // > 0 fixed, <= 0 adaptive
+  double sigma_tol;        // > 0: also require the estimated stress error <= sigma_tol
 };
 
 }  // namespace rvegpu

@@ -185,7 +185,12 @@ int build_topology(int64_t n_rve, const int64_t* node_off, const double* X, cons
         lmin = std::min(lmin, L0[e0 + e]);
         ++cnt;
       }
-      if (cnt > 255) return fail(RVE_EINVAL, at(r) + "a free node has more than 255 fibers");
+      if (cnt > 252) return fail(RVE_EINVAL, at(r) + "a free node has more than 252 fibers");
+      // pad the run to a multiple of 4 entries with the zero scratch slot (na)
+      while (cnt % 4 != 0) {
+        T.csr.push_back(uint16_t(uint32_t(na) << 1));
+        ++cnt;
+      }
       T.ncsr.push_back((begin << 8) | cnt);
       T.ncap.push_back(float(STEP_CAP * lmin));
     }
@@ -203,8 +208,8 @@ int build_topology(int64_t n_rve, const int64_t* node_off, const double* X, cons
       M.V0 = n ? (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]) : 1.0;
       if (!(M.V0 > 0.0)) M.V0 = 1.0;
     }
-    if (T.csr.size() - size_t(M.csr_off) >= (1u << 24))
-      return fail(RVE_EINVAL, at(r) + "CSR too large");
+    M.csr_len = int32_t(T.csr.size() - size_t(M.csr_off));
+    if (size_t(M.csr_len) >= (1u << 24)) return fail(RVE_EINVAL, at(r) + "CSR too large");
   }
   if (T.ncsr.size() > size_t(INT32_MAX) || T.fa.size() > size_t(INT32_MAX) || T.csr.size() > size_t(INT32_MAX))
     return fail(RVE_EINVAL, "batch too large for 32-bit offsets");

@@ -41,7 +41,7 @@ def test_options_default(rve):
     import ctypes
     o = rve._lib.rve_options()
     rve.rve_options_default(ctypes.byref(o))
-    assert o.tol == 1e-6 and o.max_iter == 200000 and o.check_every == 50
+    assert o.tol == 3e-7 and o.sigma_tol == 0.0 and o.max_iter == 200000 and o.check_every == 50
     assert o.precision == rve.RVE_PREC_MIXED and o.warm_start == 0 and o.threads == 0
 
 
