@@ -252,7 +252,8 @@ def run_ours(args, rank, world, local):
         "config": _config(),
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 9 * 8 * N_RVE,
                 "d2h_bytes_per_step": 9 * 8 * N_RVE + 2 * 4 * N_RVE},
-        "gpu_launches": int(n_bins) * args.steps,
+        # per bin and step: the longest-first sort of the work list, then the fused solve
+        "gpu_launches": 2 * int(n_bins) * args.steps,
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
