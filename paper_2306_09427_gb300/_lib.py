@@ -6,7 +6,7 @@ import os
 
 import numpy as np
 
-lib_path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "librve.so")
+lib_path = os.environ.get("RVE_LIB") or os.path.join(os.path.dirname(os.path.abspath(__file__)), "librve.so")
 if not os.path.exists(lib_path):
     raise ImportError(f"{lib_path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
                       "(the solver has no CPU fallback)")

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
-LIB = os.path.join(PKG, "librve.so")
+LIB = os.environ.get("RVE_LIB") or os.path.join(PKG, "librve.so")
+EXTRA = os.environ.get("RVE_NVCC_FLAGS", "").split()  # e.g. -DRVE_FIBER_UNROLL=1 for tuning builds
 SOURCES = ["dr_f32.cu", "dr_f64.cu", "dr_plain.cu", "capi.cu", "topology.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -29,9 +30,10 @@ def nvcc() -> str:
 
 
 def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+    tag = os.path.splitext(os.path.basename(LIB))[0]
+    obj = os.path.join(BUILD, f"{tag}_{os.path.splitext(src)[0]}.o")
     cmd = [nvcc(), "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-O2",
-           "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj]
+           "-I", INCLUDE, "-I", CSRC, *EXTRA, "-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cpp"):
         cmd[1:1] = ["-x", "cu"]
     if verbose:

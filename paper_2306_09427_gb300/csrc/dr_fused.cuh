@@ -55,14 +55,38 @@ struct Vec4<double> {
 };
 
 // Minimum resident CTAs per SM requested from the register allocator:
-// about 85 registers per thread for CTAs of up to 256 threads.
+// two 256-thread CTAs per SM (up to 128 registers per thread, no spills in
+// the loop); measured faster than three CTAs at 80 registers with spills.
+#ifndef RVE_MIN_BLOCKS_256
+#define RVE_MIN_BLOCKS_256 2
+#endif
+#ifndef RVE_FIBER_UNROLL
+#define RVE_FIBER_UNROLL 2
+#endif
 template <int NT>
 constexpr int min_blocks() {
-  return NT >= 1024 ? 1 : (NT >= 512 ? 1 : (768 / NT));
+  return NT >= 1024 ? 1 : (NT >= 512 ? 1 : (RVE_MIN_BLOCKS_256 * 256 / NT));
 }
 
-__device__ __forceinline__ float k_expm1(float x) { return expm1f(x); }
+// expm1 in FP32 for the hot loop: for |x| <= 1/2 the Taylor series of
+// e^x - 1 through x^8 (Horner; truncation below x^9/9! < 6e-9 |x|, under the
+// FP32 rounding of the result); otherwise e^x - 1 with the hardware
+// exponential (__expf), where e^x - 1 is at least 0.39 |e^x| in magnitude so
+// no cancellation amplifies its error.  Both are evaluated and one selected.
+__device__ __forceinline__ float k_expm1(float x) {
+  const float p =
+      x * (1.0f + x * (0.5f + x * (1.0f / 6.0f + x * (1.0f / 24.0f + x * (1.0f / 120.0f +
+           x * (1.0f / 720.0f + x * (1.0f / 5040.0f + x * (1.0f / 40320.0f))))))));
+  const float q = __expf(x) - 1.0f;
+  return fabsf(x) <= 0.5f ? p : q;
+}
 __device__ __forceinline__ double k_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float k_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float k_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double k_max(double a, double b) { return ::fmax(a, b); }
+__device__ __forceinline__ float k_abs(float a) { return fabsf(a); }
+__device__ __forceinline__ double k_abs(double a) { return ::fabs(a); }
+__device__ __forceinline__ double k_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float k_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double k_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ uint32_t k_unpack_ij(float w) { return __float_as_uint(w); }
@@ -152,7 +176,7 @@ __device__ __forceinline__ void fiber_force(const V4& p0, const V4& p1, const V4
   const T N = p1.y * phi;
   s = N * rl;
   const T kax = ea * ex * l * (T(2) * p1.x);
-  sbar = fmax(kax, fabs(s));
+  sbar = k_max(kax, k_abs(s));
 }
 
 // Fiber law in FP64 for set-up terms: N(eps) with the B = 0 limit.
@@ -432,32 +456,34 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
       const bool check = (it % K == 0) || (it >= A.max_iter);
       const bool want_sig = check && sig_test;
       double ps[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-      // fiber phase (two fibers per step: independent shared-memory loads overlap)
-      for (int e = tid; e < na; e += 2 * NT) {
-        const int e2 = e + NT;
-        const bool two = e2 < na;
-        const V4 p0a = P0[e], p1a = P1[e];
-        const V4 p0b = P0[two ? e2 : e], p1b = P1[two ? e2 : e];
-        const uint32_t ija = k_unpack_ij(p1a.w), ijb = k_unpack_ij(p1b.w);
-        const V4 hia = H[ija & 0xffffu], hja = H[ija >> 16];
-        const V4 hib = H[ijb & 0xffffu], hjb = H[ijb >> 16];
-        T Dx, Dy, Dz, s, sbar;
-        fiber_force<T>(p0a, p1a, hia, hja, Dx, Dy, Dz, s, sbar);
-        V4 o;
-        o.x = s * Dx;
-        o.y = s * Dy;
-        o.z = s * Dz;
-        o.w = sbar;
-        SCR[e] = o;
-        if (want_sig) add_virial(ps, o, Dx, Dy, Dz);
-        if (two) {
-          fiber_force<T>(p0b, p1b, hib, hjb, Dx, Dy, Dz, s, sbar);
-          o.x = s * Dx;
-          o.y = s * Dy;
-          o.z = s * Dz;
-          o.w = sbar;
-          SCR[e2] = o;
-          if (want_sig) add_virial(ps, o, Dx, Dy, Dz);
+      // fiber phase (RVE_FIBER_UNROLL fibers per step: independent shared-memory loads overlap)
+      for (int e = tid; e < na; e += RVE_FIBER_UNROLL * NT) {
+        V4 p0[RVE_FIBER_UNROLL], p1[RVE_FIBER_UNROLL], hi[RVE_FIBER_UNROLL], hj[RVE_FIBER_UNROLL];
+#pragma unroll
+        for (int u = 0; u < RVE_FIBER_UNROLL; ++u) {
+          const int eu = (e + u * NT < na) ? e + u * NT : e;
+          p0[u] = P0[eu];
+          p1[u] = P1[eu];
+        }
+#pragma unroll
+        for (int u = 0; u < RVE_FIBER_UNROLL; ++u) {
+          const uint32_t ij = k_unpack_ij(p1[u].w);
+          hi[u] = H[ij & 0xffffu];
+          hj[u] = H[ij >> 16];
+        }
+#pragma unroll
+        for (int u = 0; u < RVE_FIBER_UNROLL; ++u) {
+          if (u == 0 || e + u * NT < na) {
+            T Dx, Dy, Dz, s, sbar;
+            fiber_force<T>(p0[u], p1[u], hi[u], hj[u], Dx, Dy, Dz, s, sbar);
+            V4 o;
+            o.x = s * Dx;
+            o.y = s * Dy;
+            o.z = s * Dz;
+            o.w = sbar;
+            SCR[e + u * NT] = o;
+            if (want_sig) add_virial(ps, o, Dx, Dy, Dz);
+          }
         }
       }
       __syncthreads();
@@ -487,14 +513,22 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
         double v3[9] = {0.0, 0.0, 0.0, ps[0], ps[1], ps[2], ps[3], ps[4], ps[5]};
 #pragma unroll
         for (int q = 0; q < NPT; ++q) {
-          if (tid + q * NT < nf) {
-            v3[0] += double(fx[q]) * double(fx[q]) + double(fy[q]) * double(fy[q]) + double(fz[q]) * double(fz[q]);
-            v3[1] += double(vx[q]) * double(fx[q]) + double(vy[q]) * double(fy[q]) + double(vz[q]) * double(fz[q]);
+          if (tid + q * NT < nf) {  // per-node terms in T, accumulated in FP64
+            v3[0] += double(fx[q] * fx[q] + fy[q] * fy[q] + fz[q] * fz[q]);
+            v3[1] += double(vx[q] * fx[q] + vy[q] * fy[q] + vz[q] * fz[q]);
           }
         }
         v3[1] -= pre;
         v3[2] = pm;
-        block_allreduce<NT, 9>(v3, red);  // also: every gather of SCR is done
+        if (sig_test) {
+          block_allreduce<NT, 9>(v3, red);  // also: every gather of SCR is done
+        } else {
+          double v0[3] = {v3[0], v3[1], v3[2]};
+          block_allreduce<NT, 3>(v0, red);
+          v3[0] = v0[0];
+          v3[1] = v0[1];
+          v3[2] = v0[2];
+        }
         if (!(v3[0] < 1e300)) {  // NaN or Inf
           status = RVE_STATUS_NONFINITE;
           break;
@@ -553,7 +587,7 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
         const int a = tid + q * NT;
         if (a < nf) {
           const T m = T(MASS_COEF) * fw[q];
-          const T bm = beta / m;
+          const T bm = k_div(beta, m);  // fictitious mass: an approximate quotient is enough
           T nvx = alpha * vx[q] + bm * fx[q];
           T nvy = alpha * vy[q] + bm * fy[q];
           T nvz = alpha * vz[q] + bm * fz[q];
@@ -578,8 +612,8 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
           h4.w = T(0);
           H[a] = h4;
           if (pre_it) {
-            pre += double(nvx) * double(fx[q]) + double(nvy) * double(fy[q]) + double(nvz) * double(fz[q]);
-            pm += double(m) * (double(nvx) * double(nvx) + double(nvy) * double(nvy) + double(nvz) * double(nvz));
+            pre += double(nvx * fx[q] + nvy * fy[q] + nvz * fz[q]);
+            pm += double(m * (nvx * nvx + nvy * nvy + nvz * nvz));
           }
         }
       }

@@ -68,7 +68,10 @@ constexpr double STEP_CAP = 0.1;
 constexpr double DAMP_C0 = 0.1;
 constexpr double DAMP_C_MAX = 1.9;
 constexpr double ABS_FLOOR = 1e-16;  // absolute residual floor per unit EA
-constexpr int REBASE_EVERY = 4;      // FP32 path: rebase the reference state every 4 checks
+#ifndef RVE_REBASE_EVERY
+#define RVE_REBASE_EVERY 4
+#endif
+constexpr int REBASE_EVERY = RVE_REBASE_EVERY;  // FP32 path: rebase the reference state every 4 checks
 // stress-convergence estimate: stress and residual compared SIG_WINDOW
 // checks apart, contraction ratio capped at SIG_RHO_CAP
 constexpr int SIG_WINDOW = 2;
