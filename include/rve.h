@@ -28,8 +28,10 @@
  *    per item, entry 9(3i+j) + (3k+l).
  *  - Device-pointer calls are asynchronous on `stream` (a cudaStream_t,
  *    NULL = legacy default stream); outputs are valid once the stream
- *    reaches that point.  The batch object is not thread safe: serialise
- *    calls on one batch.
+ *    reaches that point.  The GPU work of each call on a batch starts after
+ *    that of the batch's previous call, whatever streams they use (they
+ *    share the batch's state).  The batch object is not thread safe:
+ *    serialise calls on one batch.
  */
 #ifndef RVE_H
 #define RVE_H
@@ -242,6 +244,52 @@ int rve_batch_get_sizes(const rve_batch* b, int32_t* free_nodes, int32_t* active
  */
 int rve_get_positions(rve_batch* b, int64_t r, const double* F, int32_t precision,
                       double* x_out);
+
+/*
+ * Continuous-batching request loop (serving).  The paper's RVE batch
+ * manager (Sec. 4.3) hands one batched solve per macroscale iteration to the
+ * GPU; the server instead takes single requests (rve id, F) as they arrive
+ * and keeps the GPU busy with overlapping waves:
+ *   - requests queue on the host in arrival order;
+ *   - each of n_slots CUDA streams, when free, launches a wave of up to
+ *     max_wave queued requests (an RVE already on the GPU waits, so its
+ *     warm-start state is advanced by one solve at a time);
+ *   - rve_server_step retires finished waves (event query, non-blocking)
+ *     and fills free slots; rve_server_drain blocks until the queue is
+ *     empty and no wave is in flight;
+ *   - rve_server_poll returns finished results in completion order with
+ *     their latency (seconds from submit to the step that saw the wave done).
+ * The batch's options apply (precision, tolerance, warm_start: with
+ * warm_start = 1 every RVE keeps its converged state on the device between
+ * requests).  The plain FP64 path allows n_slots = 1 only.
+ * Admission: RVE_EADMIT when the batch's device memory plus the server's
+ * buffers exceed hbm_cap_bytes (<= 0: no cap).  The batch must outlive the
+ * server; one host thread drives a server.  Waves of one server run
+ * concurrently (each slot has its own work buffers; an RVE is in at most one
+ * wave); call rve_server_drain before using the batch through the other
+ * rve_* calls, whose GPU work is ordered after the batch's previous call only.
+ */
+typedef struct rve_server rve_server;
+typedef struct rve_server_stats {
+  int64_t queued;       /* waiting on the host                       */
+  int64_t in_flight;    /* in waves on the GPU                       */
+  int64_t ready;        /* finished, not yet polled                  */
+  int64_t completed;    /* finished since creation                   */
+  int64_t waves;        /* waves launched since creation             */
+  int64_t device_bytes; /* device memory of the server's own buffers */
+} rve_server_stats;
+int rve_server_create(rve_server** out, rve_batch* b, int32_t n_slots, int32_t max_wave, double hbm_cap_bytes);
+/* Queue one request; F is a HOST array of 9 doubles (copied). */
+int rve_server_submit(rve_server* s, int64_t rve_id, const double* F, int64_t tag);
+int rve_server_step(rve_server* s);
+int rve_server_drain(rve_server* s);
+/* Copy up to max finished results (HOST arrays: tags[max], sigma[9 max],
+ * iters[max], status[max], latency_s[max]; any may be NULL); returns how
+ * many were copied, or a negative RVE_E* code. */
+int64_t rve_server_poll(rve_server* s, int64_t max, int64_t* tags, double* sigma, int32_t* iters,
+                        int32_t* status, double* latency_s);
+int rve_server_get_stats(const rve_server* s, rve_server_stats* st);
+void rve_server_destroy(rve_server* s);
 
 /* Free everything the batch holds (NULL is ignored). */
 void rve_batch_destroy(rve_batch* b);

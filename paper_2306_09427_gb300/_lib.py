@@ -57,6 +57,19 @@ rve_batch_get_info = _sig("rve_batch_get_info", C.c_int, [_P, C.POINTER(rve_batc
 rve_batch_get_sizes = _sig("rve_batch_get_sizes", C.c_int, [_P, _P, _P, _P])
 rve_get_positions = _sig("rve_get_positions", C.c_int, [_P, _I64, _P, _I32, _P])
 rve_batch_destroy = _sig("rve_batch_destroy", None, [_P])
+
+
+class rve_server_stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("queued", "in_flight", "ready", "completed", "waves", "device_bytes")]
+
+
+rve_server_create = _sig("rve_server_create", C.c_int, [C.POINTER(_P), _P, _I32, _I32, _D])
+rve_server_submit = _sig("rve_server_submit", C.c_int, [_P, _I64, _P, _I64])
+rve_server_step = _sig("rve_server_step", C.c_int, [_P])
+rve_server_drain = _sig("rve_server_drain", C.c_int, [_P])
+rve_server_poll = _sig("rve_server_poll", C.c_int64, [_P, _I64, _P, _P, _P, _P, _P])
+rve_server_get_stats = _sig("rve_server_get_stats", C.c_int, [_P, C.POINTER(rve_server_stats)])
+rve_server_destroy = _sig("rve_server_destroy", None, [_P])
 rve_last_error = _sig("rve_last_error", C.c_char_p, [])
 
 
@@ -219,3 +232,51 @@ class RveBatch:
         prec = self.opt.precision if precision is None else precision
         _check(rve_get_positions(self.h, r, _ptr(F), prec, _ptr(x)), "rve_get_positions")
         return x
+
+
+class RveServer:
+    """Owner of an ``rve_server`` handle (continuous batching over a batch)."""
+
+    def __init__(self, batch: RveBatch, n_slots: int = 4, max_wave: int = 1024, hbm_cap_bytes: float = 150e9):
+        self.batch = batch
+        h = _P()
+        _check(rve_server_create(C.byref(h), batch.h, n_slots, max_wave, hbm_cap_bytes), "rve_server_create")
+        self.h = h
+        self._F = np.zeros(9)
+
+    def submit(self, rve_id: int, F, tag: int) -> None:
+        self._F[:] = np.asarray(F, np.float64).reshape(9)
+        _check(rve_server_submit(self.h, rve_id, _ptr(self._F), tag), "rve_server_submit")
+
+    def step(self) -> None:
+        _check(rve_server_step(self.h), "rve_server_step")
+
+    def drain(self) -> None:
+        _check(rve_server_drain(self.h), "rve_server_drain")
+
+    def poll(self, max_items: int = 65536):
+        tags = np.empty(max_items, np.int64)
+        sigma = np.empty((max_items, 9))
+        iters = np.empty(max_items, np.int32)
+        status = np.empty(max_items, np.int32)
+        lat = np.empty(max_items)
+        n = rve_server_poll(self.h, max_items, _ptr(tags), _ptr(sigma), _ptr(iters), _ptr(status), _ptr(lat))
+        if n < 0:
+            raise RveError(int(n), "rve_server_poll")
+        return tags[:n], sigma[:n], iters[:n], status[:n], lat[:n]
+
+    def stats(self) -> dict:
+        st = rve_server_stats()
+        _check(rve_server_get_stats(self.h, C.byref(st)), "rve_server_get_stats")
+        return {n: getattr(st, n) for n, _ in rve_server_stats._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            rve_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -62,6 +62,21 @@ struct PathState {
 };
 
 constexpr int N_SIDE_STREAMS = 6;
+
+// Work-list buffers of one subset solve in flight.  Concurrent solves need
+// their own (the server gives each slot one); the batch's own set is used
+// by the public entry point, which orders itself after earlier GPU work.
+struct SubsetBuffers {
+  Work* d_work = nullptr;
+  Work* d_sorted = nullptr;
+  Work* h_stage = nullptr;  // pinned
+  size_t cap = 0;
+};
+
+// Subset solve (rve_solve_subset); fork = false keeps every launch on `s`.
+int solve_subset(rve_batch* b, const int64_t* ids, int64_t m, const double* F, double tol, int32_t max_iter,
+                 double* sigma, int32_t* iters, int32_t* status, cudaStream_t s, bool fork,
+                 const SubsetBuffers* ext);
 constexpr int N_DIRS = 18;  // 9 directions x (+h, -h)
 
 }  // namespace rvegpu
@@ -105,6 +120,7 @@ struct rve_batch {
   rvegpu::Work* h_work_pin = nullptr;  // staging for subset work lists
   size_t h_work_cap = 0;
   cudaEvent_t ev_work = nullptr;       // last upload from h_work_pin done
+  cudaEvent_t ev_last = nullptr;       // end of the last public call's GPU work on this batch
   size_t device_bytes = 0;
   std::vector<void*> allocations;
 };

@@ -286,12 +286,15 @@ int run_one(rve_batch* b, const Bin& bin, const DrArgs<T>& a, cudaStream_t s) {
 }
 
 template <typename T>
-int run_bins(rve_batch* b, const std::vector<Bin>& bins, const DrArgs<T>& a, cudaStream_t s) {
+int run_bins(rve_batch* b, const std::vector<Bin>& bins, const DrArgs<T>& a, cudaStream_t s, bool fork = true) {
   std::vector<const Bin*> live;
   for (const Bin& x : bins)
     if (x.n > 0) live.push_back(&x);
   if (live.empty()) return RVE_OK;
-  if (live.size() == 1) return run_one(b, *live[0], a, s);
+  if (live.size() == 1 || !fork) {
+    for (const Bin* x : live) TRY(run_one(b, *x, a, s));
+    return RVE_OK;
+  }
   RVE_CUDA_TRY(cudaEventRecord(b->ev_fork, s));
   const int ns = std::min<int>(N_SIDE_STREAMS, int(live.size()));
   for (int k = 0; k < ns; ++k) RVE_CUDA_TRY(cudaStreamWaitEvent(b->side[k], b->ev_fork, 0));
@@ -338,6 +341,13 @@ DrArgs<T> make_args(rve_batch* b, const double* F, double tol, int max_iter, dou
 
 int set_device(rve_batch* b) {
   RVE_CUDA_TRY(cudaSetDevice(b->device));
+  return RVE_OK;
+}
+
+// Public calls share the batch's state and scratch: each one's GPU work
+// starts after the previous call's, whatever streams they use.
+int order_after_last(rve_batch* b, cudaStream_t s) {
+  RVE_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_last, 0));
   return RVE_OK;
 }
 
@@ -538,7 +548,8 @@ int rve_batch_create(rve_batch** out, int device, int64_t n_rve, const int64_t* 
   }
   if (cudaStreamCreateWithFlags(&b->hstream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_work, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&b->ev_work, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_last, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(RVE_ECUDA, "event creation failed"));
   *out = b;
   return RVE_OK;
@@ -552,11 +563,30 @@ int rve_solve(rve_batch* b, const double* F, double tol, int32_t max_iter, doubl
   TRY(set_device(b));
   if (!(tol > 0.0)) tol = b->opt.tol;
   if (max_iter <= 0) max_iter = b->opt.max_iter;
-  return solve_all(b, F, tol, max_iter, sigma, iters, status, static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TRY(order_after_last(b, s));
+  TRY(solve_all(b, F, tol, max_iter, sigma, iters, status, s));
+  RVE_CUDA_TRY(cudaEventRecord(b->ev_last, s));
+  return RVE_OK;
 }
 
 int rve_solve_subset(rve_batch* b, const int64_t* ids, int64_t m, const double* F, double tol, int32_t max_iter,
                      double* sigma, int32_t* iters, int32_t* status, void* stream) {
+  if (!b) return fail(RVE_EINVAL, "null batch");
+  TRY(set_device(b));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TRY(order_after_last(b, s));
+  TRY(rvegpu::solve_subset(b, ids, m, F, tol, max_iter, sigma, iters, status, s, true, nullptr));
+  RVE_CUDA_TRY(cudaEventRecord(b->ev_last, s));
+  return RVE_OK;
+}
+
+}  // extern "C"
+
+namespace rvegpu {
+int solve_subset(rve_batch* b, const int64_t* ids, int64_t m, const double* F, double tol, int32_t max_iter,
+                 double* sigma, int32_t* iters, int32_t* status, cudaStream_t s, bool fork,
+                 const SubsetBuffers* ext) {
   if (!b) return fail(RVE_EINVAL, "null batch");
   if (m == 0) return RVE_OK;
   if (m < 0 || !ids || !F || !sigma) return fail(RVE_EINVAL, "bad subset arguments");
@@ -569,7 +599,6 @@ int rve_solve_subset(rve_batch* b, const int64_t* ids, int64_t m, const double* 
     if (ids[k] < 0 || ids[k] >= b->n_rve) return fail(RVE_EINVAL, "subset id out of range");
     if (seen[ids[k]]++) return fail(RVE_EINVAL, "subset ids must be distinct");
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int prec = b->opt.precision;
   if (prec == RVE_PREC_PLAIN_F64) {
     TRY(ensure_path<double>(b));
@@ -599,42 +628,54 @@ int rve_solve_subset(rve_batch* b, const int64_t* ids, int64_t m, const double* 
   for (Bin& x : bins)
     std::stable_sort(x.work.begin(), x.work.end(),
                      [&](const Work& p, const Work& q) { return b->topo.meta[p.rve].na > b->topo.meta[q.rve].na; });
-  // stage work lists: wait for the previous upload from the pinned buffer
-  if (size_t(m) > b->h_work_cap) {
-    RVE_CUDA_TRY(cudaEventSynchronize(b->ev_work));
-    if (b->h_work_pin) cudaFreeHost(b->h_work_pin);
-    b->h_work_pin = nullptr;
-    const size_t cap = std::max<size_t>(size_t(m), 1024);
-    RVE_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&b->h_work_pin), cap * sizeof(Work)));
-    b->h_work_cap = cap;
+  // stage the work lists: caller-provided buffers, or the batch's own set
+  SubsetBuffers buf;
+  if (ext) {
+    if (size_t(m) > ext->cap) return fail(RVE_EINVAL, "subset larger than the caller's work buffers");
+    buf = *ext;
+  } else {
+    RVE_CUDA_TRY(cudaEventSynchronize(b->ev_work));  // previous upload from the pinned staging done
+    if (size_t(m) > b->h_work_cap) {
+      if (b->h_work_pin) cudaFreeHost(b->h_work_pin);
+      b->h_work_pin = nullptr;
+      const size_t cap = std::max<size_t>(size_t(m), 1024);
+      RVE_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&b->h_work_pin), cap * sizeof(Work)));
+      b->h_work_cap = cap;
+    }
+    if (size_t(m) > P.sub_cap) {
+      void* p = nullptr;
+      void* q = nullptr;
+      TRY(dalloc(b, &p, std::max<size_t>(size_t(m), 1024) * sizeof(Work)));
+      TRY(dalloc(b, &q, std::max<size_t>(size_t(m), 1024) * sizeof(Work)));
+      P.d_sub_work = static_cast<Work*>(p);
+      P.d_sub_sorted = static_cast<Work*>(q);
+      P.sub_cap = std::max<size_t>(size_t(m), 1024);
+    }
+    buf.d_work = P.d_sub_work;
+    buf.d_sorted = P.d_sub_sorted;
+    buf.h_stage = b->h_work_pin;
+    buf.cap = P.sub_cap;
   }
-  if (size_t(m) > P.sub_cap) {
-    void* p = nullptr;
-    void* q = nullptr;
-    TRY(dalloc(b, &p, std::max<size_t>(size_t(m), 1024) * sizeof(Work)));
-    TRY(dalloc(b, &q, std::max<size_t>(size_t(m), 1024) * sizeof(Work)));
-    P.d_sub_work = static_cast<Work*>(p);
-    P.d_sub_sorted = static_cast<Work*>(q);
-    P.sub_cap = std::max<size_t>(size_t(m), 1024);
-  }
-  RVE_CUDA_TRY(cudaEventSynchronize(b->ev_work));
   size_t off = 0;
   for (Bin& x : bins) {
-    std::copy(x.work.begin(), x.work.end(), b->h_work_pin + off);
-    x.d_work = P.d_sub_work + off;
-    x.d_sorted = P.d_sub_sorted + off;
+    std::copy(x.work.begin(), x.work.end(), buf.h_stage + off);
+    x.d_work = buf.d_work + off;
+    x.d_sorted = buf.d_sorted + off;
     x.n = int(x.work.size());
     off += x.work.size();
   }
-  RVE_CUDA_TRY(cudaMemcpyAsync(P.d_sub_work, b->h_work_pin, off * sizeof(Work), cudaMemcpyHostToDevice, s));
-  RVE_CUDA_TRY(cudaEventRecord(b->ev_work, s));
+  RVE_CUDA_TRY(cudaMemcpyAsync(buf.d_work, buf.h_stage, off * sizeof(Work), cudaMemcpyHostToDevice, s));
+  if (!ext) RVE_CUDA_TRY(cudaEventRecord(b->ev_work, s));
   if (f32) {
     const DrArgs<float> a = make_args<float>(b, F, tol, max_iter, sigma, iters, status, b->pf.d_state, b->opt.warm_start);
-    return run_bins(b, bins, a, s);
+    return run_bins(b, bins, a, s, fork);
   }
   const DrArgs<double> a = make_args<double>(b, F, tol, max_iter, sigma, iters, status, b->pd.d_state, b->opt.warm_start);
-  return run_bins(b, bins, a, s);
+  return run_bins(b, bins, a, s, fork);
 }
+}  // namespace rvegpu
+
+extern "C" {
 
 int rve_solve_host(rve_batch* b, const double* F, double tol, int32_t max_iter, double* sigma, int32_t* iters,
                    int32_t* status) {
@@ -680,10 +721,13 @@ int rve_tangent(rve_batch* b, const double* F, double h, double tol, int32_t max
   if (!(tol > 0.0)) tol = b->opt.tol;
   if (max_iter <= 0) max_iter = b->opt.max_iter;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (b->opt.precision == RVE_PREC_MIXED) return tangent_batched<float>(b, F, h, tol, max_iter, sigma, dsigma_dF, status, s);
-  if (b->opt.precision == RVE_PREC_BATCHED_F64)
-    return tangent_batched<double>(b, F, h, tol, max_iter, sigma, dsigma_dF, status, s);
-  return fail(RVE_EINVAL, "rve_tangent needs a batched precision (RVE_PREC_MIXED or RVE_PREC_BATCHED_F64)");
+  if (b->opt.precision != RVE_PREC_MIXED && b->opt.precision != RVE_PREC_BATCHED_F64)
+    return fail(RVE_EINVAL, "rve_tangent needs a batched precision (RVE_PREC_MIXED or RVE_PREC_BATCHED_F64)");
+  TRY(order_after_last(b, s));
+  if (b->opt.precision == RVE_PREC_MIXED) TRY(tangent_batched<float>(b, F, h, tol, max_iter, sigma, dsigma_dF, status, s));
+  else TRY(tangent_batched<double>(b, F, h, tol, max_iter, sigma, dsigma_dF, status, s));
+  RVE_CUDA_TRY(cudaEventRecord(b->ev_last, s));
+  return RVE_OK;
 }
 
 int rve_reset_state(rve_batch* b, const int64_t* ids, int64_t m) {
@@ -767,6 +811,7 @@ void rve_batch_destroy(rve_batch* b) {
   if (b->hstream) cudaStreamDestroy(b->hstream);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_work) cudaEventDestroy(b->ev_work);
+  if (b->ev_last) cudaEventDestroy(b->ev_last);
   if (b->h_pl) cudaFreeHost(b->h_pl);
   if (b->h_pin) cudaFreeHost(b->h_pin);
   if (b->h_work_pin) cudaFreeHost(b->h_work_pin);
