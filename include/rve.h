@@ -84,6 +84,13 @@ typedef struct rve_batch rve_batch; /* opaque, library owned */
  *               choice, Sec. 3.2); <= 0: c re-estimated every check_every
  *               iterations from a Rayleigh quotient.  Default 0.
  *  threads      threads per CTA for the batched kernels (0 = automatic).
+ *  graphs       1: rve_solve (batched precisions, on a created stream -- the
+ *               default streams cannot be captured) records its launch
+ *               sequence as a CUDA graph on the first call with a given set
+ *               of arguments and stream, and replays it on later calls with
+ *               the same ones (e.g. the Newton iterations of a load step);
+ *               at most 16 argument sets are kept; options or bin changes
+ *               drop them.  Default 0.
  *  sigma_tol    > 0: also require the estimated remaining stress error to be
  *               <= sigma_tol at a check n: with rho = min(R_n / R_{n-2}, 0.95)
  *               the residual ratio over the last two check intervals,
@@ -101,7 +108,7 @@ typedef struct rve_options {
   int32_t warm_start;
   double damping;
   int32_t threads;
-  int32_t reserved0;
+  int32_t graphs;
   double sigma_tol;
   int32_t reserved[4];
 } rve_options;
@@ -231,6 +238,32 @@ typedef struct rve_batch_info {
   int64_t device_bytes;   /* device memory held by the batch             */
 } rve_batch_info;
 int rve_batch_get_info(const rve_batch* b, rve_batch_info* info);
+
+/*
+ * Launch configuration of the batched path, per size bin.  Bins group RVEs
+ * by footprint: resident bins (mode 0) hold a whole RVE in shared memory,
+ * streamed bins (1, 2) read fiber data from L2/HBM.
+ */
+typedef struct rve_bin_info {
+  int32_t n_rve, mode, threads, nodes_per_thread, ctas_per_sm, check_every;
+  int64_t smem_bytes;
+} rve_bin_info;
+/* Fill up to max entries for `precision` (RVE_PREC_MIXED or _BATCHED_F64);
+ * returns the number of bins (0 before the first batched solve). */
+int rve_batch_get_bins(const rve_batch* b, int32_t precision, int32_t max, rve_bin_info* out);
+
+/*
+ * Autotuner (the project's own; the paper fixes 512 threads per team,
+ * Sec. 4.3): for every size bin of the batch's precision, time solves of
+ * the bin's RVEs (cold start, deformation gradients F: device, 9 n_rve)
+ * under each thread count its RVE sizes allow and check intervals 25, 50
+ * and 100, best of `reps`, and keep the fastest configuration for the bin
+ * (the tangent's bins follow).  Synchronous.  The RVEs' warm-start state is
+ * left as after a solve.  ms_before / ms_after (may be NULL) receive the
+ * summed bin times of the old and the chosen configurations.
+ */
+int rve_autotune(rve_batch* b, const double* F, int32_t reps, void* stream, double* ms_before,
+                 double* ms_after);
 
 /* Per-RVE sizes after pruning (HOST arrays of n_rve, any may be NULL). */
 int rve_batch_get_sizes(const rve_batch* b, int32_t* free_nodes, int32_t* active_fibers,

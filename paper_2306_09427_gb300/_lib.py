@@ -20,7 +20,7 @@ RVE_PREC_PLAIN_F64, RVE_PREC_MIXED, RVE_PREC_BATCHED_F64 = 0, 1, 2
 class rve_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("check_every", C.c_int32),
                 ("precision", C.c_int32), ("warm_start", C.c_int32), ("damping", C.c_double),
-                ("threads", C.c_int32), ("reserved0", C.c_int32), ("sigma_tol", C.c_double),
+                ("threads", C.c_int32), ("graphs", C.c_int32), ("sigma_tol", C.c_double),
                 ("reserved", C.c_int32 * 4)]
 
 
@@ -56,6 +56,15 @@ rve_reset_state = _sig("rve_reset_state", C.c_int, [_P, _P, _I64])
 rve_batch_get_info = _sig("rve_batch_get_info", C.c_int, [_P, C.POINTER(rve_batch_info)])
 rve_batch_get_sizes = _sig("rve_batch_get_sizes", C.c_int, [_P, _P, _P, _P])
 rve_get_positions = _sig("rve_get_positions", C.c_int, [_P, _I64, _P, _I32, _P])
+
+
+class rve_bin_info(C.Structure):
+    _fields_ = [("n_rve", C.c_int32), ("mode", C.c_int32), ("threads", C.c_int32), ("nodes_per_thread", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("check_every", C.c_int32), ("smem_bytes", C.c_int64)]
+
+
+rve_batch_get_bins = _sig("rve_batch_get_bins", C.c_int, [_P, _I32, _I32, C.POINTER(rve_bin_info)])
+rve_autotune = _sig("rve_autotune", C.c_int, [_P, _P, _I32, _P, C.POINTER(_D), C.POINTER(_D)])
 rve_batch_destroy = _sig("rve_batch_destroy", None, [_P])
 
 
@@ -218,6 +227,22 @@ class RveBatch:
         _check(rve_tangent(self.h, _ptr(F), h, tol, max_iter, _ptr(sigma), _ptr(D), _ptr(status),
                            _stream_handle(stream)), "rve_tangent")
         return sigma, D, status
+
+    def bins(self, precision: int | None = None) -> list[dict]:
+        prec = self.opt.precision if precision is None else precision
+        arr = (rve_bin_info * 64)()
+        n = rve_batch_get_bins(self.h, prec, 64, arr)
+        if n < 0:
+            raise RveError(n, "rve_batch_get_bins")
+        return [{f: getattr(arr[i], f) for f, _ in rve_bin_info._fields_} for i in range(n)]
+
+    def autotune(self, F, reps: int = 2, stream=None) -> tuple[float, float]:
+        """Tune every bin's launch configuration on deformation gradients F (CUDA tensor);
+        returns the summed bin times (ms) before and after."""
+        before, after = C.c_double(), C.c_double()
+        _check(rve_autotune(self.h, _ptr(F), reps, _stream_handle(stream), C.byref(before), C.byref(after)),
+               "rve_autotune")
+        return before.value, after.value
 
     def reset_state(self, ids=None) -> None:
         if ids is None:

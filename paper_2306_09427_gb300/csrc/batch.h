@@ -23,6 +23,7 @@ struct Bin {
   int nt = 256;   // threads per CTA
   int npt = 1;    // free nodes per thread
   int per_sm = 1; // CTAs per SM the footprint allows (bin key)
+  int check_every = 0;  // 0: the batch option; > 0: set by the autotuner
   size_t smem = 0;
   std::vector<Work> work;
   Work* d_work = nullptr;    // canonical order
@@ -81,6 +82,20 @@ constexpr int N_DIRS = 18;  // 9 directions x (+h, -h)
 
 }  // namespace rvegpu
 
+namespace rvegpu {
+// A captured rve_solve, replayed while its arguments stay the same.
+struct GraphEntry {
+  const double* F;
+  double* sigma;
+  int32_t* iters;
+  int32_t* status;
+  cudaStream_t stream;
+  double tol;
+  int32_t max_iter;
+  cudaGraphExec_t exec;
+};
+}  // namespace rvegpu
+
 struct rve_batch {
   int device = 0;
   int64_t n_rve = 0;
@@ -123,4 +138,5 @@ struct rve_batch {
   cudaEvent_t ev_last = nullptr;       // end of the last public call's GPU work on this batch
   size_t device_bytes = 0;
   std::vector<void*> allocations;
+  std::vector<rvegpu::GraphEntry> graphs;  // rve_solve captures (option graphs = 1)
 };

@@ -65,6 +65,7 @@ int valid_options(const rve_options& o) {
   if (o.warm_start != 0 && o.warm_start != 1) return fail(RVE_EINVAL, "warm_start must be 0 or 1");
   if (!std::isfinite(o.damping)) return fail(RVE_EINVAL, "damping must be finite");
   if (!std::isfinite(o.sigma_tol)) return fail(RVE_EINVAL, "sigma_tol must be finite");
+  if (o.graphs != 0 && o.graphs != 1) return fail(RVE_EINVAL, "graphs must be 0 or 1");
   if (o.threads != 0 && o.threads != 64 && o.threads != 128 && o.threads != 256 && o.threads != 512 &&
       o.threads != 1024)
     return fail(RVE_EINVAL, "threads must be 0, 64, 128, 256, 512 or 1024");
@@ -346,6 +347,11 @@ int set_device(rve_batch* b) {
 
 // Public calls share the batch's state and scratch: each one's GPU work
 // starts after the previous call's, whatever streams they use.
+void clear_graphs(rve_batch* b) {
+  for (GraphEntry& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  b->graphs.clear();
+}
+
 int order_after_last(rve_batch* b, cudaStream_t s) {
   RVE_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_last, 0));
   return RVE_OK;
@@ -453,6 +459,96 @@ int tangent_batched(rve_batch* b, const double* F, double h, double tol, int max
   return RVE_OK;
 }
 
+// Autotuner: per bin, time the bin's RVEs under each launch configuration
+// their sizes allow and keep the fastest.
+template <typename T>
+int autotune_path(rve_batch* b, const double* F, int reps, cudaStream_t s, double* ms_before, double* ms_after) {
+  TRY(ensure_path<T>(b));
+  PathState& P = path<T>(b);
+  double* d_sig = nullptr;
+  int32_t *d_it = nullptr, *d_st = nullptr;
+  RVE_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_sig), sizeof(double) * 9 * size_t(b->n_rve), s));
+  RVE_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_it), sizeof(int32_t) * size_t(b->n_rve), s));
+  RVE_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_st), sizeof(int32_t) * size_t(b->n_rve), s));
+  cudaEvent_t e0, e1;
+  RVE_CUDA_TRY(cudaEventCreate(&e0));
+  RVE_CUDA_TRY(cudaEventCreate(&e1));
+  DrArgs<T> a = make_args<T>(b, F, b->opt.tol, b->opt.max_iter, d_sig, d_it, d_st, P.d_state, 0);
+  auto time_bin = [&](const Bin& bin, float& ms) -> int {
+    float best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+      RVE_CUDA_TRY(cudaEventRecord(e0, s));
+      TRY(run_one(b, bin, a, s));
+      RVE_CUDA_TRY(cudaEventRecord(e1, s));
+      RVE_CUDA_TRY(cudaEventSynchronize(e1));
+      float t = 0.f;
+      RVE_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+      best = std::min(best, t);
+    }
+    ms = best;
+    return RVE_OK;
+  };
+  double before = 0.0, after = 0.0;
+  for (Bin& bin : P.bins) {
+    if (bin.n == 0) continue;
+    int nf_max = 0, na_max = 0, csr_max = 0;
+    for (const Work& w : bin.work) {
+      nf_max = std::max(nf_max, b->topo.meta[w.rve].nf);
+      na_max = std::max(na_max, b->topo.meta[w.rve].na);
+      csr_max = std::max(csr_max, b->topo.meta[w.rve].csr_len);
+    }
+    float t_cur = 0.f;
+    TRY(run_one(b, bin, a, s));  // warm-up (attributes, caches)
+    TRY(time_bin(bin, t_cur));
+    before += t_cur;
+    Bin best = bin;
+    float t_best = t_cur;
+    for (int nt : {64, 128, 256, 512, 1024}) {
+      BinKey k;
+      if (choose_key<T>(nf_max, na_max, csr_max, nt, k) != RVE_OK) continue;
+      if (k.mode != bin.mode || k.nt != nt) continue;  // same storage mode, the asked thread count
+      for (int kc : {25, 50, 100}) {
+        Bin cand = bin;
+        cand.nt = k.nt;
+        cand.npt = k.npt;
+        cand.per_sm = k.per_sm;
+        cand.smem = std::max(k.smem, size_t(0));
+        cand.check_every = kc;
+        float t = 0.f;
+        TRY(run_one(b, cand, a, s));
+        TRY(time_bin(cand, t));
+        if (t < t_best) {
+          t_best = t;
+          best = cand;
+        }
+      }
+    }
+    bin.nt = best.nt;
+    bin.npt = best.npt;
+    bin.per_sm = best.per_sm;
+    bin.smem = best.smem;
+    bin.check_every = best.check_every;
+    after += t_best;
+  }
+  // the tangent bins mirror the solve bins' configurations
+  for (size_t j = 0; j < P.tan_bins.size() && j < P.bins.size(); ++j) {
+    P.tan_bins[j].nt = P.bins[j].nt;
+    P.tan_bins[j].npt = P.bins[j].npt;
+    P.tan_bins[j].per_sm = P.bins[j].per_sm;
+    P.tan_bins[j].smem = P.bins[j].smem;
+    P.tan_bins[j].check_every = P.bins[j].check_every;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  RVE_CUDA_TRY(cudaFreeAsync(d_sig, s));
+  RVE_CUDA_TRY(cudaFreeAsync(d_it, s));
+  RVE_CUDA_TRY(cudaFreeAsync(d_st, s));
+  RVE_CUDA_TRY(cudaStreamSynchronize(s));
+  if (ms_before) *ms_before = before;
+  if (ms_after) *ms_after = after;
+  return RVE_OK;
+}
+
 }  // namespace
 }  // namespace rvegpu
 
@@ -480,6 +576,7 @@ int rve_set_options(rve_batch* b, const rve_options* opt) {
   TRY(valid_options(*opt));
   const bool retune = opt->threads != b->opt.threads;
   b->opt = *opt;
+  clear_graphs(b);  // options are baked into captured launches
   if (retune) {
     b->pf.ready = false;  // bins depend on the thread count; rebuilt lazily
     b->pd.ready = false;
@@ -565,8 +662,43 @@ int rve_solve(rve_batch* b, const double* F, double tol, int32_t max_iter, doubl
   if (max_iter <= 0) max_iter = b->opt.max_iter;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   TRY(order_after_last(b, s));
+  // graphs need a created stream (the legacy and per-thread default streams cannot be captured)
+  const bool graphable = b->opt.graphs && b->opt.precision != RVE_PREC_PLAIN_F64 && s != nullptr &&
+                         s != cudaStreamLegacy && s != cudaStreamPerThread;
+  if (graphable) {
+    for (const GraphEntry& g : b->graphs)
+      if (g.F == F && g.sigma == sigma && g.iters == iters && g.status == status && g.stream == s && g.tol == tol &&
+          g.max_iter == max_iter) {
+        RVE_CUDA_TRY(cudaGraphLaunch(g.exec, s));
+        RVE_CUDA_TRY(cudaEventRecord(b->ev_last, s));
+        return RVE_OK;
+      }
+  }
   TRY(solve_all(b, F, tol, max_iter, sigma, iters, status, s));
   RVE_CUDA_TRY(cudaEventRecord(b->ev_last, s));
+  if (graphable && b->graphs.size() < 16) {
+    // record the same launch sequence (nothing runs during capture) for replay
+    // relaxed mode: only stream work is recorded; the host-side calls of the
+    // launch path (error queries, attributes) stay legal during capture
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      (void)cudaGetLastError();  // not capturable: the solve above already ran uncaptured
+      return RVE_OK;
+    }
+    const int rc = solve_all(b, F, tol, max_iter, sigma, iters, status, s);
+    const cudaError_t ce = cudaStreamEndCapture(s, &g);  // always leave capture mode
+    if (rc != RVE_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      (void)cudaGetLastError();  // do not leak the capture's error into later calls
+      if (rc != RVE_OK) return rc;
+      return fail(RVE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return fail(RVE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    b->graphs.push_back(GraphEntry{F, sigma, iters, status, s, tol, max_iter, exec});
+  }
   return RVE_OK;
 }
 
@@ -748,6 +880,44 @@ int rve_reset_state(rve_batch* b, const int64_t* ids, int64_t m) {
   return RVE_OK;
 }
 
+int rve_autotune(rve_batch* b, const double* F, int32_t reps, void* stream, double* ms_before, double* ms_after) {
+  if (!b || !F) return fail(RVE_EINVAL, "batch and F are required");
+  if (b->n_rve == 0) return RVE_OK;
+  if (reps < 1) reps = 1;
+  TRY(set_device(b));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TRY(order_after_last(b, s));
+  int rc;
+  clear_graphs(b);  // bin configurations are baked into captured launches
+  if (b->opt.precision == RVE_PREC_MIXED) rc = autotune_path<float>(b, F, reps, s, ms_before, ms_after);
+  else if (b->opt.precision == RVE_PREC_BATCHED_F64) rc = autotune_path<double>(b, F, reps, s, ms_before, ms_after);
+  else return fail(RVE_EINVAL, "the autotuner tunes the batched precisions");
+  if (rc != RVE_OK) return rc;
+  RVE_CUDA_TRY(cudaEventRecord(b->ev_last, s));
+  return RVE_OK;
+}
+
+int rve_batch_get_bins(const rve_batch* b, int32_t precision, int32_t max, rve_bin_info* out) {
+  if (!b) return fail(RVE_EINVAL, "null batch");
+  const PathState& P = precision == RVE_PREC_BATCHED_F64 ? b->pd : b->pf;
+  if (!P.ready) return 0;
+  int n = 0;
+  for (const Bin& x : P.bins) {
+    if (n >= max) break;
+    if (out) {
+      out[n].n_rve = x.n;
+      out[n].mode = x.mode;
+      out[n].threads = x.nt;
+      out[n].nodes_per_thread = x.npt;
+      out[n].ctas_per_sm = x.per_sm;
+      out[n].check_every = x.check_every > 0 ? x.check_every : b->opt.check_every;
+      out[n].smem_bytes = int64_t(x.smem);
+    }
+    ++n;
+  }
+  return n;
+}
+
 int rve_batch_get_info(const rve_batch* b, rve_batch_info* info) {
   if (!b || !info) return fail(RVE_EINVAL, "null argument");
   info->n_rve = b->n_rve;
@@ -803,6 +973,7 @@ void rve_batch_destroy(rve_batch* b) {
   if (!b) return;
   cudaSetDevice(b->device);
   cudaDeviceSynchronize();
+  clear_graphs(b);
   for (void* p : b->allocations) cudaFree(p);
   for (int k = 0; k < N_SIDE_STREAMS; ++k) {
     if (b->side[k]) cudaStreamDestroy(b->side[k]);

@@ -19,6 +19,7 @@ int launch_variant(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
   DrArgs<T> b = a;
   b.work = bin.d_work;
   b.n_work = bin.n;
+  if (bin.check_every > 0) b.check_every = bin.check_every;
   fn<<<bin.n, NT, bin.smem, s>>>(b);
   RVE_CUDA_TRY(cudaGetLastError());
   return RVE_OK;

@@ -1,0 +1,72 @@
+"""Batch scheduling: CUDA-graph replay and the autotuner (GPU)."""
+import numpy as np
+import pytest
+
+import rvegen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rve():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2306_09427_gb300 as rve
+    return rve
+
+
+def _F(F):
+    import torch
+    return torch.tensor(np.asarray(F).reshape(-1, 9), dtype=torch.float64, device="cuda:0")
+
+
+def test_graph_replay_matches_plain_launches(rve):
+    import torch
+    nets, Fs = rvegen.config_uneven(48, side_hi=11)
+    pk = rvegen.pack(nets)
+    ref = rve.RveBatch(pk, precision=rve.RVE_PREC_MIXED)
+    gb = rve.RveBatch(pk, precision=rve.RVE_PREC_MIXED, graphs=1)
+    Fd = _F(Fs)
+    sig = torch.empty((48, 9), dtype=torch.float64, device="cuda:0")
+    it = torch.empty(48, dtype=torch.int32, device="cuda:0")
+    st = torch.empty(48, dtype=torch.int32, device="cuda:0")
+    s0, i0, _ = ref.solve(Fd)
+    stream = torch.cuda.Stream()  # graphs need a created stream
+    torch.cuda.synchronize()
+    for _ in range(3):  # first call runs and records, the others replay
+        gb.solve(Fd, sigma=sig, iters=it, status=st, stream=stream)
+        torch.cuda.synchronize()
+        assert torch.equal(sig, s0) and torch.equal(it, i0)
+    F2 = Fs + 0.003 * np.eye(3)
+    Fd.copy_(_F(F2))  # same pointer, new contents: the replay reads them
+    torch.cuda.synchronize()
+    gb.solve(Fd, sigma=sig, iters=it, status=st, stream=stream)
+    s2, _, _ = ref.solve(_F(F2))
+    torch.cuda.synchronize()
+    assert torch.equal(sig, s2)
+    ref.close()
+    gb.close()
+
+
+def test_autotuner_keeps_results(rve):
+    nets, Fs = rvegen.config_uneven(96, side_hi=12)
+    b = rve.RveBatch(rvegen.pack(nets), precision=rve.RVE_PREC_MIXED)
+    Fd = _F(Fs)
+    s0, _, st0 = b.solve(Fd)
+    before_bins = b.bins()
+    t_before, t_after = b.autotune(Fd, reps=1)
+    after_bins = b.bins()
+    assert t_after <= t_before * 1.05
+    assert len(after_bins) == len(before_bins)
+    for x in after_bins:
+        assert x["threads"] in (64, 128, 256, 512, 1024) and x["check_every"] in (25, 50, 100) or x["n_rve"] == 0
+    s1, _, st1 = b.solve(Fd)
+    s0, s1 = s0.cpu().numpy(), s1.cpu().numpy()
+    assert (st1.cpu().numpy() == 0).all()
+    e = np.linalg.norm(s1 - s0, axis=1) / np.linalg.norm(s0, axis=1)
+    print("autotune: %.2f -> %.2f ms; sigma change max %.2e" % (t_before, t_after, e.max()))
+    assert (e <= 1e-4).mean() >= 0.95
+    b.close()
