@@ -373,6 +373,7 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
     const uint2* csr_g = reinterpret_cast<const uint2*>(A.csr + M.csr_off);
     for (int k = tid; k < M.csr_len / 4; k += NT) csr_s[k] = csr_g[k];
   }
+  const uint32_t zero_run = (uint32_t(na) << 1) | (uint32_t(na) << 17);  // two entries at the zero slot
   if (tid == 0) {  // zero slot that padded CSR entries point at
     V4 z;
     z.x = z.y = z.z = z.w = T(0);
@@ -452,8 +453,10 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
   int status = RVE_STATUS_EMPTY;
   if (nf > 0 && !badF) {
     status = RVE_STATUS_MAX_ITER;
+    int to_check = 0;  // iterations until the next check (it % K without a division)
     for (;; ++it) {
-      const bool check = (it % K == 0) || (it >= A.max_iter);
+      const bool check = (to_check == 0) || (it >= A.max_iter);
+      to_check = (to_check == 0) ? K - 1 : to_check - 1;
       const bool want_sig = check && sig_test;
       double ps[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
       // fiber phase (RVE_FIBER_UNROLL fibers per step: independent shared-memory loads overlap)
@@ -487,24 +490,45 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
         }
       }
       __syncthreads();
-      // gather
+      // gather: the first run of 4 CSR entries of every owned node is loaded
+      // unconditionally (a free node keeps >= 2 fibers, its run is padded to 4
+      // with the zero slot), so all owned nodes' loads are in flight together;
+      // nodes with more than 4 fibers continue in a loop.
       T fx[NPT], fy[NPT], fz[NPT], fw[NPT];
+      {
+        uint2 pk[NPT];
 #pragma unroll
-      for (int q = 0; q < NPT; ++q) {
-        fx[q] = fy[q] = fz[q] = fw[q] = T(0);
-        const int a = tid + q * NT;
-        if (a < nf) {
-          const uint32_t b = cs[q] >> 8, n = cs[q] & 0xffu;  // n is a multiple of 4
-          for (uint32_t k = 0; k < n; k += 4) {
-            const uint2 pk = *reinterpret_cast<const uint2*>(CSR + b + k);
-            const uint32_t e0 = pk.x & 0xffffu, e1 = pk.x >> 16, e2 = pk.y & 0xffffu, e3 = pk.y >> 16;
-            const V4 s0 = SCR[e0 >> 1], s1 = SCR[e1 >> 1], s2 = SCR[e2 >> 1], s3 = SCR[e3 >> 1];
-            const T g0 = (e0 & 1u) ? T(-1) : T(1), g1 = (e1 & 1u) ? T(-1) : T(1);
-            const T g2 = (e2 & 1u) ? T(-1) : T(1), g3 = (e3 & 1u) ? T(-1) : T(1);
-            fx[q] += g0 * s0.x + g1 * s1.x + g2 * s2.x + g3 * s3.x;
-            fy[q] += g0 * s0.y + g1 * s1.y + g2 * s2.y + g3 * s3.y;
-            fz[q] += g0 * s0.z + g1 * s1.z + g2 * s2.z + g3 * s3.z;
-            fw[q] += (s0.w + s1.w) + (s2.w + s3.w);
+        for (int q = 0; q < NPT; ++q) {
+          const int a = tid + q * NT;
+          pk[q] = (a < nf) ? *reinterpret_cast<const uint2*>(CSR + (cs[q] >> 8)) : make_uint2(zero_run, zero_run);
+        }
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+          const uint32_t e0 = pk[q].x & 0xffffu, e1 = pk[q].x >> 16, e2 = pk[q].y & 0xffffu, e3 = pk[q].y >> 16;
+          const V4 s0 = SCR[e0 >> 1], s1 = SCR[e1 >> 1], s2 = SCR[e2 >> 1], s3 = SCR[e3 >> 1];
+          const T g0 = (e0 & 1u) ? T(-1) : T(1), g1 = (e1 & 1u) ? T(-1) : T(1);
+          const T g2 = (e2 & 1u) ? T(-1) : T(1), g3 = (e3 & 1u) ? T(-1) : T(1);
+          fx[q] = g0 * s0.x + g1 * s1.x + g2 * s2.x + g3 * s3.x;
+          fy[q] = g0 * s0.y + g1 * s1.y + g2 * s2.y + g3 * s3.y;
+          fz[q] = g0 * s0.z + g1 * s1.z + g2 * s2.z + g3 * s3.z;
+          fw[q] = (s0.w + s1.w) + (s2.w + s3.w);
+        }
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+          const int a = tid + q * NT;
+          if (a < nf) {
+            const uint32_t b = cs[q] >> 8, n = cs[q] & 0xffu;  // n is a multiple of 4
+            for (uint32_t k = 4; k < n; k += 4) {
+              const uint2 p2 = *reinterpret_cast<const uint2*>(CSR + b + k);
+              const uint32_t e0 = p2.x & 0xffffu, e1 = p2.x >> 16, e2 = p2.y & 0xffffu, e3 = p2.y >> 16;
+              const V4 s0 = SCR[e0 >> 1], s1 = SCR[e1 >> 1], s2 = SCR[e2 >> 1], s3 = SCR[e3 >> 1];
+              const T g0 = (e0 & 1u) ? T(-1) : T(1), g1 = (e1 & 1u) ? T(-1) : T(1);
+              const T g2 = (e2 & 1u) ? T(-1) : T(1), g3 = (e3 & 1u) ? T(-1) : T(1);
+              fx[q] += g0 * s0.x + g1 * s1.x + g2 * s2.x + g3 * s3.x;
+              fy[q] += g0 * s0.y + g1 * s1.y + g2 * s2.y + g3 * s3.y;
+              fz[q] += g0 * s0.z + g1 * s1.z + g2 * s2.z + g3 * s3.z;
+              fw[q] += (s0.w + s1.w) + (s2.w + s3.w);
+            }
           }
         }
       }
@@ -580,7 +604,7 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
         ++n_checks;
         do_rebase = std::is_same<T, float>::value && (n_checks % REBASE_EVERY == 0);
       }
-      const bool pre_it = adaptive && ((it + 1) % K == 0);
+      const bool pre_it = adaptive && (to_check == 0);  // the iteration before a check
       // update owned nodes
 #pragma unroll
       for (int q = 0; q < NPT; ++q) {
