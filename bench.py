@@ -57,9 +57,11 @@ def _dist():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms; only samples
+    whose timestamps fall inside the timed window [t0, t1] (host wall clock)
+    are summarised."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
@@ -70,12 +72,13 @@ class ClockSampler:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.p = None
 
-    def stop(self):
+    def stop(self, t0: float = 0.0, t1: float = float("inf")):
+        import datetime
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
@@ -88,18 +91,21 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if not (t0 <= ts <= t1):
+                    continue
+                sm.append(float(f[2]))
+                smax.append(float(f[3]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
+            for nm, v in zip(names, f[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples inside the timed window"]}
         loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
         return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
                 "samples": len(sm)}
@@ -172,7 +178,6 @@ def run_ours(args, rank, world, local):
     nets, Fs = rvegen.config_uniform(N_RVE, side=SIDE, first=rank * N_RVE)
     pk = rvegen.pack(nets)
     b = rve.RveBatch(pk, device=local, precision=rve.RVE_PREC_MIXED, tol=TOL, sigma_tol=SIGMA_TOL, warm_start=0)
-    info = b.info()
     Fd = torch.tensor(Fs.reshape(-1, 9), dtype=torch.float64, device=dev)
     sigma = torch.empty((N_RVE, 9), dtype=torch.float64, device=dev)
     iters = torch.empty(N_RVE, dtype=torch.int32, device=dev)
@@ -188,11 +193,15 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     n_bins = b.info()["n_bins"]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    info = b.info()  # after the first solve: the size bins exist
     clk = ClockSampler(local)
     clk.start()
+    time.sleep(1.0)  # nvidia-smi start-up, so that samples cover the timed window
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    b.set_kernel_timing(True)  # events around each fused-kernel launch, on its launching stream
+    t_win0 = time.time()
     it_total = 0
     for k in range(args.steps):
         flush.zero_()
@@ -200,8 +209,10 @@ def run_ours(args, rank, world, local):
         step()
         ev[k][1].record(stream)
     torch.cuda.synchronize()
-    clocks = clk.stop()
+    clocks = clk.stop(t_win0, time.time())
     step_ms = [a.elapsed_time(z) for a, z in ev]
+    kernel_ms = b.last_kernel_ms()  # n_bins launches per step
+    b.set_kernel_timing(False)
     t_total = sum(step_ms) / 1e3
     it = iters.cpu().numpy()
     st = status.cpu().numpy()
@@ -216,11 +227,14 @@ def run_ours(args, rank, world, local):
     fiber_updates = float((na.astype(np.float64) * it).sum())
     node_updates = float((nf.astype(np.float64) * it).sum())
     t_step = t_total / args.steps
+    # the dominant kernel: the fused solve; with one bin it is one launch per step,
+    # with several (concurrent) bins their summed durations bound the kernel time
+    t_kernel = float(kernel_ms.sum()) / 1e3 / args.steps
     flops = FLOPS_PER_FIBER_UPDATE * fiber_updates + FLOPS_PER_NODE_UPDATE * node_updates
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clocks.get("sm_mhz") or 2070.0
     peak = sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-    achieved = flops / t_step / 1e12
+    achieved = flops / t_kernel / 1e12
 
     # end to end through the public host-buffer call (copies inside)
     e2e_steps = max(1, min(args.steps, 5))
@@ -257,6 +271,7 @@ def run_ours(args, rank, world, local):
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
+                     "kernel_ms_per_launch": float(kernel_ms.mean()), "launches_timed": int(kernel_ms.size),
                      "kernel": "dr_fused_kernel<float,...> (one CTA per RVE, resident in shared memory)",
                      "peak_note": f"FP32 FMA peak derived: {sm_count} SMs x 128 lanes x 2 flops x {mhz:.0f} MHz "
                                   "(median SM clock under load)"},
@@ -304,7 +319,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for the CPU baseline")

@@ -265,6 +265,27 @@ int rve_batch_get_bins(const rve_batch* b, int32_t precision, int32_t max, rve_b
 int rve_autotune(rve_batch* b, const double* F, int32_t reps, void* stream, double* ms_before,
                  double* ms_after);
 
+/*
+ * Launch timing of the fused DR kernel (measurement aid, Sec. 5's timings).
+ * With on = 1, every launch of the fused solve kernel is bracketed by two
+ * CUDA events recorded on the stream that launches it (the caller's stream,
+ * or an internal side stream when several bins run concurrently), and
+ * rve_solve is not captured into or replayed from a CUDA graph.  Every call
+ * clears the record; launches of all later calls (solve, subset, host solve,
+ * tangent, autotune) are appended, up to 65536.  Returns RVE_EINVAL for on
+ * not 0 or 1.
+ */
+int rve_set_kernel_timing(rve_batch* b, int32_t on);
+
+/*
+ * Durations (ms, HOST array of at least max doubles) of the fused-kernel
+ * launches recorded since timing was last switched, in launch order; waits
+ * for those launches to finish.  Returns the number of launches recorded
+ * (it may exceed max; only the first max are written), or a negative error
+ * code.
+ */
+int rve_last_kernel_ms(rve_batch* b, int32_t max, double* ms);
+
 /* Per-RVE sizes after pruning (HOST arrays of n_rve, any may be NULL). */
 int rve_batch_get_sizes(const rve_batch* b, int32_t* free_nodes, int32_t* active_fibers,
                         int32_t* fixed_fibers);

@@ -65,6 +65,8 @@ class rve_bin_info(C.Structure):
 
 rve_batch_get_bins = _sig("rve_batch_get_bins", C.c_int, [_P, _I32, _I32, C.POINTER(rve_bin_info)])
 rve_autotune = _sig("rve_autotune", C.c_int, [_P, _P, _I32, _P, C.POINTER(_D), C.POINTER(_D)])
+rve_set_kernel_timing = _sig("rve_set_kernel_timing", C.c_int, [_P, _I32])
+rve_last_kernel_ms = _sig("rve_last_kernel_ms", C.c_int, [_P, _I32, _P])
 rve_batch_destroy = _sig("rve_batch_destroy", None, [_P])
 
 
@@ -243,6 +245,20 @@ class RveBatch:
         _check(rve_autotune(self.h, _ptr(F), reps, _stream_handle(stream), C.byref(before), C.byref(after)),
                "rve_autotune")
         return before.value, after.value
+
+    def set_kernel_timing(self, on: bool = True) -> None:
+        _check(rve_set_kernel_timing(self.h, 1 if on else 0), "rve_set_kernel_timing")
+
+    def last_kernel_ms(self) -> np.ndarray:
+        """Durations (ms) of the fused-kernel launches since timing was last switched."""
+        n = rve_last_kernel_ms(self.h, 0, None)
+        if n < 0:
+            raise RveError(n, "rve_last_kernel_ms")
+        out = np.zeros(max(n, 1), np.float64)
+        m = rve_last_kernel_ms(self.h, n, out.ctypes.data_as(C.c_void_p))
+        if m < 0:
+            raise RveError(m, "rve_last_kernel_ms")
+        return out[:n]
 
     def reset_state(self, ids=None) -> None:
         if ids is None:

@@ -139,4 +139,8 @@ struct rve_batch {
   size_t device_bytes = 0;
   std::vector<void*> allocations;
   std::vector<rvegpu::GraphEntry> graphs;  // rve_solve captures (option graphs = 1)
+  // optional per-launch timing of the fused solve kernel (rve_set_kernel_timing)
+  bool timing = false;
+  std::vector<cudaEvent_t> kev;  // start/end pairs, reused across calls
+  size_t n_kev = 0;              // pairs recorded by the last public call
 };

@@ -279,11 +279,29 @@ int ensure_path(rve_batch* b) {
 }
 
 // Run a list of bins on `s`, concurrently on side streams when there are several.
+constexpr size_t KERNEL_TIMING_MAX = 65536;  // launches recorded per rve_set_kernel_timing
+
 template <typename T>
 int run_one(rve_batch* b, const Bin& bin, const DrArgs<T>& a, cudaStream_t s) {
   Bin use;
   TRY(launch_sorted(b, bin, s, a.last_iters, use));
-  return launch_bin(a, use, s);
+  if (!b->timing || b->n_kev >= KERNEL_TIMING_MAX) return launch_bin(a, use, s);
+  // events on the launching stream bracket the fused kernel alone
+  if (2 * b->n_kev + 2 > b->kev.size()) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    RVE_CUDA_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      return fail(RVE_ECUDA, "cudaEventCreate failed");
+    }
+    b->kev.push_back(e0);
+    b->kev.push_back(e1);
+  }
+  const size_t k = 2 * b->n_kev++;
+  RVE_CUDA_TRY(cudaEventRecord(b->kev[k], s));
+  TRY(launch_bin(a, use, s));
+  RVE_CUDA_TRY(cudaEventRecord(b->kev[k + 1], s));
+  return RVE_OK;
 }
 
 template <typename T>
@@ -662,8 +680,9 @@ int rve_solve(rve_batch* b, const double* F, double tol, int32_t max_iter, doubl
   if (max_iter <= 0) max_iter = b->opt.max_iter;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   TRY(order_after_last(b, s));
-  // graphs need a created stream (the legacy and per-thread default streams cannot be captured)
-  const bool graphable = b->opt.graphs && b->opt.precision != RVE_PREC_PLAIN_F64 && s != nullptr &&
+  // graphs need a created stream (the legacy and per-thread default streams cannot be captured);
+  // kernel timing records events between launches, so it runs uncaptured
+  const bool graphable = b->opt.graphs && !b->timing && b->opt.precision != RVE_PREC_PLAIN_F64 && s != nullptr &&
                          s != cudaStreamLegacy && s != cudaStreamPerThread;
   if (graphable) {
     for (const GraphEntry& g : b->graphs)
@@ -862,6 +881,28 @@ int rve_tangent(rve_batch* b, const double* F, double h, double tol, int32_t max
   return RVE_OK;
 }
 
+int rve_set_kernel_timing(rve_batch* b, int32_t on) {
+  if (!b) return fail(RVE_EINVAL, "null batch");
+  if (on != 0 && on != 1) return fail(RVE_EINVAL, "on must be 0 or 1");
+  b->timing = on != 0;
+  b->n_kev = 0;
+  return RVE_OK;
+}
+
+int rve_last_kernel_ms(rve_batch* b, int32_t max, double* ms) {
+  if (!b) return fail(RVE_EINVAL, "null batch");
+  if (max > 0 && !ms) return fail(RVE_EINVAL, "ms is required when max > 0");
+  TRY(set_device(b));
+  const int32_t n = int32_t(b->n_kev);
+  for (int32_t k = 0; k < n && k < max; ++k) {
+    RVE_CUDA_TRY(cudaEventSynchronize(b->kev[2 * size_t(k) + 1]));
+    float t = 0.0f;
+    RVE_CUDA_TRY(cudaEventElapsedTime(&t, b->kev[2 * size_t(k)], b->kev[2 * size_t(k) + 1]));
+    ms[k] = double(t);
+  }
+  return n;
+}
+
 int rve_reset_state(rve_batch* b, const int64_t* ids, int64_t m) {
   if (!b) return fail(RVE_EINVAL, "null batch");
   TRY(set_device(b));
@@ -974,6 +1015,7 @@ void rve_batch_destroy(rve_batch* b) {
   cudaSetDevice(b->device);
   cudaDeviceSynchronize();
   clear_graphs(b);
+  for (cudaEvent_t e : b->kev) cudaEventDestroy(e);
   for (void* p : b->allocations) cudaFree(p);
   for (int k = 0; k < N_SIDE_STREAMS; ++k) {
     if (b->side[k]) cudaStreamDestroy(b->side[k]);

@@ -70,3 +70,25 @@ def test_autotuner_keeps_results(rve):
     print("autotune: %.2f -> %.2f ms; sigma change max %.2e" % (t_before, t_after, e.max()))
     assert (e <= 1e-4).mean() >= 0.95
     b.close()
+
+
+def test_kernel_timing_records_every_launch(rve):
+    import torch
+    nets, Fs = rvegen.config_uneven(40, side_hi=11)
+    b = rve.RveBatch(rvegen.pack(nets), precision=rve.RVE_PREC_MIXED, graphs=1)
+    Fd = _F(Fs)
+    stream = torch.cuda.Stream()
+    s0, _, _ = b.solve(Fd, stream=stream)
+    n_bins = sum(1 for x in b.bins() if x["n_rve"] > 0)
+    b.set_kernel_timing(True)
+    for _ in range(3):
+        s1, _, _ = b.solve(Fd, stream=stream)  # timing forces uncaptured launches
+    t = b.last_kernel_ms()
+    assert t.shape == (3 * n_bins,) and (t > 0).all() and np.isfinite(t).all()
+    torch.cuda.synchronize()
+    assert torch.equal(s0, s1)
+    b.set_kernel_timing(False)
+    assert b.last_kernel_ms().shape == (0,)
+    b.solve(Fd, stream=stream)
+    assert b.last_kernel_ms().shape == (0,)
+    b.close()
