@@ -111,11 +111,19 @@ struct CSum {
   }
 };
 
+__device__ __forceinline__ float warp_sum_t(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+__device__ __forceinline__ double warp_sum_t(double v) { return warp_sum(v); }
 
 __device__ __forceinline__ void warp_csum(double& s, double& c) {
 #pragma unroll
@@ -256,12 +264,11 @@ __device__ __forceinline__ void rebase(const DrArgs<T>& A, const Work& wk, const
     const double gx = sF[0] * q.dx + sF[1] * q.dy + sF[2] * q.dz + (HR[3 * j + 0] - HR[3 * i + 0]);
     const double gy = sF[3] * q.dx + sF[4] * q.dy + sF[5] * q.dz + (HR[3 * j + 1] - HR[3 * i + 1]);
     const double gz = sF[6] * q.dx + sF[7] * q.dy + sF[8] * q.dz + (HR[3 * j + 2] - HR[3 * i + 2]);
-    const double L02 = q.L0 * q.L0;
     V4 p0;
     p0.x = T(gx);
     p0.y = T(gy);
     p0.z = T(gz);
-    p0.w = T(0.5 * (gx * gx + gy * gy + gz * gz - L02) / L02);
+    p0.w = T((gx * gx + gy * gy + gz * gz - q.L0 * q.L0) * q.half_inv_L02);
     P0[e] = p0;
   }
   __syncthreads();
@@ -276,6 +283,9 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
   // loop-carried block-uniform scalars kept in shared memory, not registers
   // (thresholds; previous stress and residual, double-buffered by check parity)
   __shared__ double sThr[2], sSig[SIG_WINDOW + 1][8];
+  // decisions of a check, published by thread 0: outcome and damping factors
+  __shared__ int sFlag;
+  __shared__ T sAB[2];
 
   const Work wk = A.work[blockIdx.x];
   const RveMeta M = A.meta[wk.rve];
@@ -438,7 +448,11 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
   const bool adaptive = !(A.damping > 0.0);
   double c = adaptive ? DAMP_C0 : A.damping;
   T alpha = T((2.0 - c) / (2.0 + c)), beta = T(2.0 / (2.0 + c));
-  double pre = 0.0, pm = 0.0;  // thread partials from the iteration before a check
+  if (tid == 0) {
+    sAB[0] = alpha;
+    sAB[1] = beta;
+  }
+  T pre = T(0), pm = T(0);  // thread partials from the iteration before a check
   bool have_pre = false;
   int it = 0, n_checks = 0;
   // stress-convergence test: below thr_tight the residual alone decides
@@ -534,72 +548,115 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
       }
       bool do_rebase = false;
       if (check) {
-        double v3[9] = {0.0, 0.0, 0.0, ps[0], ps[1], ps[2], ps[3], ps[4], ps[5]};
+        // Per-thread and per-warp partials in the loop type T; the per-warp
+        // partials are summed in FP64 by warp 0, whose lane 0 takes every
+        // block-uniform decision once (convergence, damping) and publishes it
+        // in shared memory.  The stress-test sums stay in FP64 throughout.
+        T t3[3] = {T(0), T(0), pm};
 #pragma unroll
         for (int q = 0; q < NPT; ++q) {
-          if (tid + q * NT < nf) {  // per-node terms in T, accumulated in FP64
-            v3[0] += double(fx[q] * fx[q] + fy[q] * fy[q] + fz[q] * fz[q]);
-            v3[1] += double(vx[q] * fx[q] + vy[q] * fy[q] + vz[q] * fz[q]);
+          if (tid + q * NT < nf) {
+            t3[0] += fx[q] * fx[q] + fy[q] * fy[q] + fz[q] * fz[q];
+            t3[1] += vx[q] * fx[q] + vy[q] * fy[q] + vz[q] * fz[q];
           }
         }
-        v3[1] -= pre;
-        v3[2] = pm;
-        if (sig_test) {
-          block_allreduce<NT, 9>(v3, red);  // also: every gather of SCR is done
-        } else {
-          double v0[3] = {v3[0], v3[1], v3[2]};
-          block_allreduce<NT, 3>(v0, red);
-          v3[0] = v0[0];
-          v3[1] = v0[1];
-          v3[2] = v0[2];
-        }
-        if (!(v3[0] < 1e300)) {  // NaN or Inf
-          status = RVE_STATUS_NONFINITE;
-          break;
-        }
-        bool sig_ok = true;
-        if (sig_test && v3[0] > sThr[1]) {
-          // remaining stress error of a geometrically converging sequence, from
-          // the stress and residual SIG_WINDOW checks back (ring of records)
-          const double* prev = sSig[(n_checks + 1) % (SIG_WINDOW + 1)];
-          double* next = sSig[n_checks % (SIG_WINDOW + 1)];
-          const double r = sqrt(v3[0]);
-          double dn = 0.0, nn = 0.0;
+        t3[1] -= pre;
+        const int warp = tid >> 5, lane = tid & 31;
 #pragma unroll
-          for (int k = 0; k < 6; ++k) {
-            const double sg = v3[3 + k] + sBB[2 * k] + sBB[2 * k + 1];
-            const double wk2 = k < 3 ? 1.0 : 2.0;  // off-diagonal entries appear twice
-            dn += wk2 * (sg - prev[k]) * (sg - prev[k]);
-            nn += wk2 * sg * sg;
-            if (tid == 0) next[k] = sg;
-          }
-          sig_ok = false;
-          if (prev[7] != 0.0 && nn > 0.0) {
-            const double rho = fmin(r / prev[6], SIG_RHO_CAP);
-            sig_ok = sqrt(dn / nn) * rho / (1.0 - rho) <= A.sigma_tol;
-          }
-          if (tid == 0) {
-            next[6] = r;
-            next[7] = 1.0;
-          }
-        } else if (sig_test && tid == 0) {
-          sSig[n_checks % (SIG_WINDOW + 1)][7] = 0.0;
+        for (int k = 0; k < 3; ++k) t3[k] = warp_sum_t(t3[k]);
+        if (sig_test) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) ps[k] = warp_sum(ps[k]);
         }
-        if (v3[0] <= sThr[0] && sig_ok) {
-          status = RVE_STATUS_CONVERGED;
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) red[warp * 9 + k] = double(t3[k]);
+          if (sig_test) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) red[warp * 9 + 3 + k] = ps[k];
+          }
+        }
+        __syncthreads();
+        if (warp == 0) {
+          constexpr int NW = NT / 32;
+          double v3[9];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) v3[k] = 0.0;
+          if (lane < NW) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v3[k] = red[lane * 9 + k];
+            if (sig_test) {
+#pragma unroll
+              for (int k = 3; k < 9; ++k) v3[k] = red[lane * 9 + k];
+            }
+          }
+#pragma unroll
+          for (int o = NW / 2; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v3[k] += __shfl_xor_sync(0xffffffffu, v3[k], o);
+            if (sig_test) {
+#pragma unroll
+              for (int k = 3; k < 9; ++k) v3[k] += __shfl_xor_sync(0xffffffffu, v3[k], o);
+            }
+          }
+          if (lane == 0) {
+            int flag = -1;  // keep iterating; otherwise the final status
+            if (!(v3[0] < 1e300)) {  // NaN or Inf
+              flag = RVE_STATUS_NONFINITE;
+            } else {
+              bool sig_ok = true;
+              if (sig_test && v3[0] > sThr[1]) {
+                // remaining stress error of a geometrically converging sequence, from
+                // the stress and residual SIG_WINDOW checks back (ring of records)
+                const double* prev = sSig[(n_checks + 1) % (SIG_WINDOW + 1)];
+                double* next = sSig[n_checks % (SIG_WINDOW + 1)];
+                const double r = sqrt(v3[0]);
+                double dn = 0.0, nn = 0.0;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                  const double sg = v3[3 + k] + sBB[2 * k] + sBB[2 * k + 1];
+                  const double wk2 = k < 3 ? 1.0 : 2.0;  // off-diagonal entries appear twice
+                  dn += wk2 * (sg - prev[k]) * (sg - prev[k]);
+                  nn += wk2 * sg * sg;
+                  next[k] = sg;
+                }
+                sig_ok = false;
+                if (prev[7] != 0.0 && nn > 0.0) {
+                  const double rho = fmin(r / prev[6], SIG_RHO_CAP);
+                  sig_ok = sqrt(dn / nn) * rho / (1.0 - rho) <= A.sigma_tol;
+                }
+                next[6] = r;
+                next[7] = 1.0;
+              } else if (sig_test) {
+                sSig[n_checks % (SIG_WINDOW + 1)][7] = 0.0;
+              }
+              if (v3[0] <= sThr[0] && sig_ok) {
+                flag = RVE_STATUS_CONVERGED;
+              } else if (it >= A.max_iter) {
+                flag = RVE_STATUS_MAX_ITER;
+              } else if (adaptive && have_pre && v3[2] > 0.0) {
+                const double lam = -v3[1] / v3[2];
+                if (lam > 0.0) {
+                  c = fmin(2.0 * sqrt(lam), DAMP_C_MAX);
+                  sAB[0] = T((2.0 - c) / (2.0 + c));
+                  sAB[1] = T(2.0 / (2.0 + c));
+                }
+              }
+            }
+            sFlag = flag;
+          }
+        }
+        __syncthreads();
+        const int flag = sFlag;
+        if (flag == RVE_STATUS_NONFINITE || flag == RVE_STATUS_CONVERGED) {
+          status = flag;
           break;
         }
-        if (it >= A.max_iter) break;
-        if (adaptive && have_pre && v3[2] > 0.0) {
-          const double lam = -v3[1] / v3[2];
-          if (lam > 0.0) {
-            c = fmin(2.0 * sqrt(lam), DAMP_C_MAX);
-            alpha = T((2.0 - c) / (2.0 + c));
-            beta = T(2.0 / (2.0 + c));
-          }
-        }
-        pre = 0.0;
-        pm = 0.0;
+        if (flag == RVE_STATUS_MAX_ITER) break;  // status is already RVE_STATUS_MAX_ITER
+        alpha = sAB[0];
+        beta = sAB[1];
+        pre = T(0);
+        pm = T(0);
         have_pre = false;
         ++n_checks;
         do_rebase = std::is_same<T, float>::value && (n_checks % REBASE_EVERY == 0);
@@ -636,8 +693,8 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
           h4.w = T(0);
           H[a] = h4;
           if (pre_it) {
-            pre += double(nvx * fx[q] + nvy * fy[q] + nvz * fz[q]);
-            pm += double(m * (nvx * nvx + nvy * nvy + nvz * nvz));
+            pre += nvx * fx[q] + nvy * fy[q] + nvz * fz[q];
+            pm += m * (nvx * nvx + nvy * nvy + nvz * nvz);
           }
         }
       }

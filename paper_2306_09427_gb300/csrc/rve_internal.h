@@ -21,6 +21,7 @@ namespace rvegpu {
 struct FibD {
   double dx, dy, dz;  // X_j - X_i (reference chord)
   double L0, EA, B;
+  double half_inv_L02;  // 1 / (2 L0^2): Green strain without a division on the device
 };
 
 // Per-RVE metadata, one per RVE on the device.

@@ -303,7 +303,8 @@ int build_topology(int64_t n_rve, const int64_t* node_off, const double* X, cons
       }
       sum_ea += EA[e0 + e];
       const FibD f{Xr[3 * b] - Xr[3 * a], Xr[3 * b + 1] - Xr[3 * a + 1], Xr[3 * b + 2] - Xr[3 * a + 2],
-                   L0[e0 + e], EA[e0 + e], B[e0 + e]};
+                   L0[e0 + e], EA[e0 + e], B[e0 + e],
+                   0.5 / (L0[e0 + e] * L0[e0 + e])};
       if (nb[a] && nb[b]) {
         T.fb.push_back(f);
         ++nbf;
