@@ -39,6 +39,10 @@ PLAIN_SUBSET = 32   # RVEs timed on the plain FP64 per-RVE path
 FLOPS_PER_FIBER_UPDATE = 47.0
 FLOPS_PER_NODE_UPDATE = 17.0   # lumped mass, damped velocity, cap, position
 FP32_LANES_PER_SM = 128
+# dram__bytes_read.sum + dram__bytes_write.sum of one fused-kernel launch on
+# this workload (ncu capture summarised in profiles/dr_fused_uniform1024_full.md);
+# None whenever the kernel changes after that capture
+TRAFFIC_BYTES_PER_LAUNCH = 105.43e6 + 5.84e6
 
 
 def _config():
@@ -270,7 +274,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": 2 * int(n_bins) * args.steps,
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_LAUNCH, "traffic_unit": "bytes per launch",
                      "kernel_ms_per_launch": float(kernel_ms.mean()), "launches_timed": int(kernel_ms.size),
                      "kernel": "dr_fused_kernel<float,...> (one CTA per RVE, resident in shared memory)",
                      "peak_note": f"FP32 FMA peak derived: {sm_count} SMs x 128 lanes x 2 flops x {mhz:.0f} MHz "
