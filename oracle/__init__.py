@@ -28,6 +28,7 @@ from .fiber_law import axial_force, axial_stiffness, fiber_energy
 from .network import convergence_threshold, prune, reference_force_scale
 from .newton import Solution, solve
 from .tangent import dsigma_dF
+from .mandel import mandel_tangent
 
 __all__ = ["axial_force", "axial_stiffness", "fiber_energy", "prune",
-           "reference_force_scale", "convergence_threshold", "Solution", "solve", "dsigma_dF"]
+           "reference_force_scale", "convergence_threshold", "Solution", "solve", "dsigma_dF", "mandel_tangent"]
