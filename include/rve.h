@@ -223,6 +223,28 @@ int rve_solve_plain_noalloc(rve_batch* b, int64_t r, const double* F, double tol
 int rve_tangent(rve_batch* b, const double* F, double h, double tol, int32_t max_iter,
                 double* sigma, double* dsigma_dF, int32_t* status, void* stream);
 
+/*
+ * The paper's material tangent (Sec. 3.2, Eqs. tensor_fd and
+ * stiffness-push-forward): with F = R U, six forward-difference solves of
+ * the second Piola-Kirchhoff stress Pi = J F^-1 sigma F^-T along the
+ * probing directions T_p (the columns of the paper's Mandel matrix [T]),
+ *   P_ij,p = (Pi_ij(R (U + h T_p)) - Pi_ij(F)) / h,
+ * run as six solves per RVE in one launch per bin, warm-started from the
+ * base solution (Pi depends on U only, so R (U + h T_p) probes U + h T_p);
+ * [A] from [A][M][T] = [P] with M = dE/dU; and the spatial stiffness
+ * C_mnpq = J^-1 F_mi F_nj A_ijrs F_pr F_qs.  Post-processing in FP64 on
+ * the device, one thread per RVE.  h <= 0 means 1e-4.
+ *   F       device 9*n_rve; sigma device 9*n_rve (stress at F);
+ *   C       device 36*n_rve: the 6x6 Mandel matrix of C per RVE, row-major,
+ *           index order (11, 22, 33, 23, 13, 12), shear rows and columns
+ *           scaled by sqrt(2);
+ *   status  device n_rve (worst over the 7 solves; RVE_STATUS_NONFINITE if
+ *           [M][T] is singular) or NULL.
+ * Needs RVE_PREC_MIXED or RVE_PREC_BATCHED_F64 (RVE_EINVAL otherwise).
+ */
+int rve_tangent_mandel(rve_batch* b, const double* F, double h, double tol, int32_t max_iter,
+                       double* sigma, double* C, int32_t* status, void* stream);
+
 /* Forget the warm-start state of the m RVEs in ids (HOST array); ids ==
  * NULL resets every RVE.  Synchronous. */
 int rve_reset_state(rve_batch* b, const int64_t* ids, int64_t m);

@@ -111,12 +111,18 @@ def push_forward(F, A):
     return np.einsum("mi,nj,ijrs,pr,qs->mnpq", F, F, A, F, F) / np.linalg.det(F)
 
 
-def mandel_tangent(X, conn, L0, EA, B, is_boundary, F, V0=1.0, h=1e-6, tol=1e-12):
-    """Returns (sigma at F, [A] 6x6, [C] 6x6) by the paper's six-solve procedure."""
+def mandel_tangent(X, conn, L0, EA, B, is_boundary, F, V0=1.0, h=1e-6, tol=1e-12, h0_U=None):
+    """Returns (sigma at F, [A] 6x6, [C] 6x6) by the paper's six-solve procedure.
+
+    ``h0_U`` (N,3) optionally warm-starts the base solve at U (a fluctuation
+    x - U X), so that the tangent is taken at a given equilibrium when the
+    network has several stable ones."""
     F = np.asarray(F, np.float64).reshape(3, 3)
     Xr = np.asarray(X, np.float64).reshape(-1, 3)
     R, U = polar(F)                                                           # step 1
-    base = solve(X, conn, L0, EA, B, is_boundary, U, V0=V0, tol=tol)
+    base = solve(X, conn, L0, EA, B, is_boundary, U, V0=V0, tol=tol, h0=h0_U)
+    if not base.stable:
+        raise ValueError("base state is not a stable equilibrium")
     Pi0 = pk2(U, base.sigma)
     h0 = base.x - Xr @ U.T
     Tm = T_mandel()

@@ -52,6 +52,7 @@ rve_solve_host = _sig("rve_solve_host", C.c_int, [_P, _P, _D, _I32, _P, _P, _P])
 rve_solve_plain_noalloc = _sig("rve_solve_plain_noalloc", C.c_int, [_P, _I64, _P, _D, _I32, _P, _P, _P, _P])
 RVE_NOALLOC_MAX_ACTIVE_FIBERS, RVE_NOALLOC_MAX_FREE_NODES = 16384, 8192
 rve_tangent = _sig("rve_tangent", C.c_int, [_P, _P, _D, _D, _I32, _P, _P, _P, _P])
+rve_tangent_mandel = _sig("rve_tangent_mandel", C.c_int, [_P, _P, _D, _D, _I32, _P, _P, _P, _P])
 rve_reset_state = _sig("rve_reset_state", C.c_int, [_P, _P, _I64])
 rve_batch_get_info = _sig("rve_batch_get_info", C.c_int, [_P, C.POINTER(rve_batch_info)])
 rve_batch_get_sizes = _sig("rve_batch_get_sizes", C.c_int, [_P, _P, _P, _P])
@@ -229,6 +230,17 @@ class RveBatch:
         _check(rve_tangent(self.h, _ptr(F), h, tol, max_iter, _ptr(sigma), _ptr(D), _ptr(status),
                            _stream_handle(stream)), "rve_tangent")
         return sigma, D, status
+
+    def tangent_mandel(self, F, h: float = 1e-4, tol: float = 0.0, max_iter: int = 0, stream=None):
+        """The paper's six-solve tangent: returns (sigma (n, 9), C (n, 6, 6) Mandel, status)."""
+        import torch
+        n = self.n_rve
+        sigma = torch.empty((n, 9), dtype=torch.float64, device=F.device)
+        Cm = torch.empty((n, 6, 6), dtype=torch.float64, device=F.device)
+        status = torch.empty(n, dtype=torch.int32, device=F.device)
+        _check(rve_tangent_mandel(self.h, _ptr(F), h, tol, max_iter, _ptr(sigma), _ptr(Cm), _ptr(status),
+                                  _stream_handle(stream)), "rve_tangent_mandel")
+        return sigma, Cm, status
 
     def bins(self, precision: int | None = None) -> list[dict]:
         prec = self.opt.precision if precision is None else precision

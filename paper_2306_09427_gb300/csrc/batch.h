@@ -47,6 +47,7 @@ struct PathState {
   std::vector<BinKey> key_of;   // per RVE
   std::vector<Bin> bins;        // all-RVE solve
   std::vector<Bin> tan_bins;    // tangent: 18 perturbed solves per RVE
+  std::vector<Bin> man_bins;    // six-solve (Mandel) tangent: direction slots 0..5 of the above
   void* d_state = nullptr;      // 4 doubles per free node (fluctuation h, FP64 for both paths)
   uint8_t* d_valid = nullptr;   // per RVE: state holds a previous solve
   int32_t* d_last_iters = nullptr;  // per RVE: iterations of its last solve (scheduling cost)

@@ -8,6 +8,7 @@
 
 #include "batch.h"
 #include "dr_fused.cuh"
+#include "mandel.cuh"
 
 namespace rvegpu {
 
@@ -226,6 +227,7 @@ int ensure_path(rve_batch* b) {
   if (scr_tan > INT32_MAX) return fail(RVE_EINVAL, "streamed scratch exceeds 32-bit offsets");
   P.bins.clear();
   P.tan_bins.clear();
+  P.man_bins.clear();
   for (size_t j = 0; j < keys.size(); ++j) {
     std::vector<int>& mem = members[j];
     std::stable_sort(mem.begin(), mem.end(),
@@ -237,13 +239,18 @@ int ensure_path(rve_batch* b) {
     bin.per_sm = keys[j].per_sm;
     bin.smem = keys[j].smem;
     Bin tb = bin;
+    Bin mb = bin;
     for (int r : mem) bin.work.push_back(Work{r, r, b->topo.meta[r].node_off, 0, scr_of[r], 0});
     for (int r : mem)
-      for (int d = 0; d < N_DIRS; ++d)
-        tb.work.push_back(Work{r, int32_t(d * n + r), int32_t(d * b->total_nf + b->topo.meta[r].node_off), 1,
-                               int32_t(scr_tan_of[r] + d * (b->topo.meta[r].na + 1)), 0});
+      for (int d = 0; d < N_DIRS; ++d) {
+        const Work w{r, int32_t(d * n + r), int32_t(d * b->total_nf + b->topo.meta[r].node_off), 1,
+                     int32_t(scr_tan_of[r] + d * (b->topo.meta[r].na + 1)), 0};
+        tb.work.push_back(w);
+        if (d < N_MANDEL) mb.work.push_back(w);
+      }
     P.bins.push_back(std::move(bin));
     P.tan_bins.push_back(std::move(tb));
+    P.man_bins.push_back(std::move(mb));
   }
   // largest total work first so the long bins start early
   auto work_of = [&](const Bin& x) {
@@ -254,6 +261,8 @@ int ensure_path(rve_batch* b) {
   std::stable_sort(P.bins.begin(), P.bins.end(), [&](const Bin& x, const Bin& y) { return work_of(x) > work_of(y); });
   std::stable_sort(P.tan_bins.begin(), P.tan_bins.end(),
                    [&](const Bin& x, const Bin& y) { return work_of(x) > work_of(y); });
+  std::stable_sort(P.man_bins.begin(), P.man_bins.end(),
+                   [&](const Bin& x, const Bin& y) { return work_of(x) > work_of(y); });
   P.bin_of.assign(size_t(n), -1);
   P.work_of.assign(size_t(n), Work{});
   for (size_t j = 0; j < P.bins.size(); ++j)
@@ -263,6 +272,7 @@ int ensure_path(rve_batch* b) {
     }
   TRY(upload_bins(b, P.bins));
   TRY(upload_bins(b, P.tan_bins));
+  TRY(upload_bins(b, P.man_bins));
   TRY(dalloc(b, &P.d_state, sizeof(double) * 4 * size_t(std::max<int64_t>(b->total_nf, 1))));
   RVE_CUDA_TRY(cudaMemset(P.d_state, 0, sizeof(double) * 4 * size_t(std::max<int64_t>(b->total_nf, 1))));
   TRY(dalloc(b, reinterpret_cast<void**>(&P.d_valid), size_t(std::max<int64_t>(n, 1))));
@@ -394,9 +404,10 @@ int solve_all(rve_batch* b, const double* F, double tol, int max_iter, double* s
   return RVE_OK;
 }
 
-__global__ void tan_copy_state(const double* __restrict__ st, double* __restrict__ tan, int64_t total_nf) {
+__global__ void tan_copy_state(const double* __restrict__ st, double* __restrict__ tan, int64_t total_nf,
+                               int n_dirs) {
   const int64_t n4 = 4 * total_nf;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < int64_t(N_DIRS) * n4;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < int64_t(n_dirs) * n4;
        i += int64_t(gridDim.x) * blockDim.x)
     tan[i] = st[i % n4];
 }
@@ -427,11 +438,11 @@ __global__ void tan_finish(const double* __restrict__ S, const int32_t* __restri
   }
 }
 
+// Buffers of the perturbed solves (both tangents): F, sigma, iterations and
+// status per direction slot, the slots' warm-start states, and the streamed
+// bins' scratch (laid out for all 18 slots; the six-solve tangent uses 0..5).
 template <typename T>
-int tangent_batched(rve_batch* b, const double* F, double h, double tol, int max_iter, double* sigma,
-                    double* dsdF, int32_t* status, cudaStream_t s) {
-  TRY(ensure_path<T>(b));
-  PathState& P = path<T>(b);
+int tangent_buffers(rve_batch* b, PathState& P, DrArgs<T>& a1) {
   const int64_t n = b->n_rve;
   if (!b->d_tanF) {
     TRY(dalloc(b, reinterpret_cast<void**>(&b->d_tanF), sizeof(double) * 9 * N_DIRS * size_t(n)));
@@ -441,23 +452,6 @@ int tangent_batched(rve_batch* b, const double* F, double h, double tol, int max
   }
   if (!P.d_tan_state)
     TRY(dalloc(b, &P.d_tan_state, sizeof(double) * 4 * N_DIRS * size_t(std::max<int64_t>(b->total_nf, 1))));
-  int32_t* st_base = status ? status : b->d_tanSt + N_DIRS * n;
-  int32_t* it_base = b->d_tanI + N_DIRS * n;
-  // base solve
-  const DrArgs<T> a0 = make_args<T>(b, F, tol, max_iter, sigma, it_base, st_base, P.d_state, b->opt.warm_start);
-  TRY(run_bins(b, P.bins, a0, s));
-  // perturbed solves, warm-started from the base fluctuation
-  if (b->total_nf > 0) {
-    tan_copy_state<<<1024, 256, 0, s>>>(static_cast<const double*>(P.d_state), static_cast<double*>(P.d_tan_state),
-                                        b->total_nf);
-    RVE_CUDA_TRY(cudaGetLastError());
-  }
-  if (n > 0) {
-    tan_make_F<<<256, 256, 0, s>>>(F, b->d_tanF, n, h);
-    RVE_CUDA_TRY(cudaGetLastError());
-  }
-  DrArgs<T> a1 = make_args<T>(b, b->d_tanF, tol, max_iter, b->d_tanS, b->d_tanI, b->d_tanSt, P.d_tan_state, 1);
-  // the tangent bins have their own streamed scratch (18 directions per RVE)
   int64_t scr = 0;
   for (const Bin& bin : P.tan_bins)
     if (bin.mode != 0)
@@ -469,6 +463,75 @@ int tangent_batched(rve_batch* b, const double* F, double h, double tol, int max
     a1.gP1 = static_cast<T*>(P.d_tan_g[1]);
     a1.gSCR = static_cast<T*>(P.d_tan_g[2]);
   }
+  return RVE_OK;
+}
+
+// The paper's six-solve tangent (Sec. 3.2): base solve at F, six probing
+// solves at R (U + h T_p) warm-started from it, then the FP64 algebra of
+// mandel_finish.  C: 36 doubles per RVE (Mandel [I][J]).
+template <typename T>
+int mandel_batched(rve_batch* b, const double* F, double h, double tol, int max_iter, double* sigma, double* C,
+                   int32_t* status, cudaStream_t s) {
+  TRY(ensure_path<T>(b));
+  PathState& P = path<T>(b);
+  const int64_t n = b->n_rve;
+  DrArgs<T> a1 = make_args<T>(b, nullptr, tol, max_iter, nullptr, nullptr, nullptr, nullptr, 1);
+  TRY(tangent_buffers<T>(b, P, a1));
+  int32_t* st_base = status ? status : b->d_tanSt + N_DIRS * n;
+  int32_t* it_base = b->d_tanI + N_DIRS * n;
+  const DrArgs<T> a0 = make_args<T>(b, F, tol, max_iter, sigma, it_base, st_base, P.d_state, b->opt.warm_start);
+  TRY(run_bins(b, P.bins, a0, s));
+  if (b->total_nf > 0) {
+    tan_copy_state<<<1024, 256, 0, s>>>(static_cast<const double*>(P.d_state), static_cast<double*>(P.d_tan_state),
+                                        b->total_nf, N_MANDEL);
+    RVE_CUDA_TRY(cudaGetLastError());
+  }
+  if (n > 0) {
+    mandel_make_F<<<int((n + 127) / 128 < 4096 ? (n + 127) / 128 : 4096), 128, 0, s>>>(F, b->d_tanF, n, h);
+    RVE_CUDA_TRY(cudaGetLastError());
+  }
+  a1.F = b->d_tanF;
+  a1.sigma = b->d_tanS;
+  a1.iters = b->d_tanI;
+  a1.status = b->d_tanSt;
+  a1.state = static_cast<double*>(P.d_tan_state);
+  TRY(run_bins(b, P.man_bins, a1, s));
+  if (n > 0) {
+    mandel_finish<<<int((n + 127) / 128 < 4096 ? (n + 127) / 128 : 4096), 128, 0, s>>>(
+        F, sigma, b->d_tanS, b->d_tanSt, n, h, C, status);
+    RVE_CUDA_TRY(cudaGetLastError());
+  }
+  return RVE_OK;
+}
+
+template <typename T>
+int tangent_batched(rve_batch* b, const double* F, double h, double tol, int max_iter, double* sigma,
+                    double* dsdF, int32_t* status, cudaStream_t s) {
+  TRY(ensure_path<T>(b));
+  PathState& P = path<T>(b);
+  const int64_t n = b->n_rve;
+  DrArgs<T> a1 = make_args<T>(b, nullptr, tol, max_iter, nullptr, nullptr, nullptr, nullptr, 1);
+  TRY(tangent_buffers<T>(b, P, a1));
+  int32_t* st_base = status ? status : b->d_tanSt + N_DIRS * n;
+  int32_t* it_base = b->d_tanI + N_DIRS * n;
+  // base solve
+  const DrArgs<T> a0 = make_args<T>(b, F, tol, max_iter, sigma, it_base, st_base, P.d_state, b->opt.warm_start);
+  TRY(run_bins(b, P.bins, a0, s));
+  // perturbed solves, warm-started from the base fluctuation
+  if (b->total_nf > 0) {
+    tan_copy_state<<<1024, 256, 0, s>>>(static_cast<const double*>(P.d_state), static_cast<double*>(P.d_tan_state),
+                                        b->total_nf, N_DIRS);
+    RVE_CUDA_TRY(cudaGetLastError());
+  }
+  if (n > 0) {
+    tan_make_F<<<256, 256, 0, s>>>(F, b->d_tanF, n, h);
+    RVE_CUDA_TRY(cudaGetLastError());
+  }
+  a1.F = b->d_tanF;
+  a1.sigma = b->d_tanS;
+  a1.iters = b->d_tanI;
+  a1.status = b->d_tanSt;
+  a1.state = static_cast<double*>(P.d_tan_state);
   TRY(run_bins(b, P.tan_bins, a1, s));
   if (n > 0) {
     tan_finish<<<512, 256, 0, s>>>(b->d_tanS, b->d_tanSt, n, h, dsdF, status);
@@ -549,13 +612,14 @@ int autotune_path(rve_batch* b, const double* F, int reps, cudaStream_t s, doubl
     after += t_best;
   }
   // the tangent bins mirror the solve bins' configurations
-  for (size_t j = 0; j < P.tan_bins.size() && j < P.bins.size(); ++j) {
-    P.tan_bins[j].nt = P.bins[j].nt;
-    P.tan_bins[j].npt = P.bins[j].npt;
-    P.tan_bins[j].per_sm = P.bins[j].per_sm;
-    P.tan_bins[j].smem = P.bins[j].smem;
-    P.tan_bins[j].check_every = P.bins[j].check_every;
-  }
+  for (std::vector<Bin>* tb : {&P.tan_bins, &P.man_bins})
+    for (size_t j = 0; j < tb->size() && j < P.bins.size(); ++j) {
+      (*tb)[j].nt = P.bins[j].nt;
+      (*tb)[j].npt = P.bins[j].npt;
+      (*tb)[j].per_sm = P.bins[j].per_sm;
+      (*tb)[j].smem = P.bins[j].smem;
+      (*tb)[j].check_every = P.bins[j].check_every;
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   RVE_CUDA_TRY(cudaFreeAsync(d_sig, s));
@@ -901,6 +965,25 @@ int rve_last_kernel_ms(rve_batch* b, int32_t max, double* ms) {
     ms[k] = double(t);
   }
   return n;
+}
+
+int rve_tangent_mandel(rve_batch* b, const double* F, double h, double tol, int32_t max_iter, double* sigma,
+                       double* C, int32_t* status, void* stream) {
+  if (!b) return fail(RVE_EINVAL, "null batch");
+  if (b->n_rve == 0) return RVE_OK;
+  if (!F || !sigma || !C) return fail(RVE_EINVAL, "F, sigma and C are required");
+  TRY(set_device(b));
+  if (!(h > 0.0)) h = 1e-4;
+  if (!(tol > 0.0)) tol = b->opt.tol;
+  if (max_iter <= 0) max_iter = b->opt.max_iter;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (b->opt.precision != RVE_PREC_MIXED && b->opt.precision != RVE_PREC_BATCHED_F64)
+    return fail(RVE_EINVAL, "rve_tangent_mandel needs a batched precision (RVE_PREC_MIXED or RVE_PREC_BATCHED_F64)");
+  TRY(order_after_last(b, s));
+  if (b->opt.precision == RVE_PREC_MIXED) TRY(mandel_batched<float>(b, F, h, tol, max_iter, sigma, C, status, s));
+  else TRY(mandel_batched<double>(b, F, h, tol, max_iter, sigma, C, status, s));
+  RVE_CUDA_TRY(cudaEventRecord(b->ev_last, s));
+  return RVE_OK;
 }
 
 int rve_reset_state(rve_batch* b, const int64_t* ids, int64_t m) {

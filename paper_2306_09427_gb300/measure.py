@@ -2,7 +2,7 @@
 
     python -m paper_2306_09427_gb300.measure single    # one 6^3 RVE, F = I + 0.1 e1 (x) e1
     python -m paper_2306_09427_gb300.measure uneven    # 4096 RVEs, side 6..16, p 0.5..0.8
-    python -m paper_2306_09427_gb300.measure tangent   # 32,000 8^3 RVEs, sigma + dsigma/dF
+    python -m paper_2306_09427_gb300.measure tangent   # 32,000 8^3 RVEs, sigma + dsigma/dF, and the six-solve C
 
 Each line gives the batched mixed-precision path (one solve of the whole
 batch, CUDA events on a created stream, warm-up excluded, median of the
@@ -30,7 +30,10 @@ def _time_solves(b, Fd, reps, stream, tangent=False):
     for k in range(reps + 2):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res = b.tangent(Fd, stream=stream) if tangent else b.solve(Fd, stream=stream)
+        if tangent == "mandel":
+            res = b.tangent_mandel(Fd, stream=stream)
+        else:
+            res = b.tangent(Fd, stream=stream) if tangent else b.solve(Fd, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
         if k >= 2:
@@ -85,6 +88,10 @@ def run(config: str, reps: int = 5, plain_subset: int = 32, tol: float = 3e-7, a
         st = st.cpu().numpy()
         res.update(tangent_s=dt, rve_tangents_per_s=n / dt, rve_solves_per_s=19 * n / dt,
                    converged_frac=float((st == 0).mean()))
+        # the paper's six-solve tangent (7 solves per RVE) on the same batch
+        dtm, (_, _, stm) = _time_solves(b, Fd, reps, stream, tangent="mandel")
+        res.update(mandel_tangent_s=dtm, mandel_tangents_per_s=n / dtm,
+                   mandel_converged_frac=float((stm.cpu().numpy() == 0).mean()))
     else:
         if autotune and config == "uneven":
             before, after = b.autotune(Fd, reps=1, stream=stream)
