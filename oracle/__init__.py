@@ -29,6 +29,7 @@ from .network import convergence_threshold, prune, reference_force_scale
 from .newton import Solution, solve
 from .tangent import dsigma_dF
 from .mandel import mandel_tangent
+from .orientation import orientation_tensor, p2
 
 __all__ = ["axial_force", "axial_stiffness", "fiber_energy", "prune",
-           "reference_force_scale", "convergence_threshold", "Solution", "solve", "dsigma_dF", "mandel_tangent"]
+           "reference_force_scale", "convergence_threshold", "Solution", "solve", "dsigma_dF", "mandel_tangent", "orientation_tensor", "p2"]
