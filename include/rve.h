@@ -308,6 +308,22 @@ int rve_set_kernel_timing(rve_batch* b, int32_t on);
  */
 int rve_last_kernel_ms(rve_batch* b, int32_t max, double* ms);
 
+/*
+ * Orientation tensor of every RVE (Sec. 4 sends it to the macroscale;
+ * Sec. 5 measures alignment by P2 = <3 cos^2(theta) - 1>/2):
+ *   Omega = <n (x) n>, n = (x_j - x_i)/|x_j - x_i|,
+ * averaged over the fibers kept after pruning (active and boundary-to-
+ * boundary), at x = F X + h with h the state left by the last solve in
+ * `precision` (h = 0 for an RVE not yet solved in it).  P2 along a unit
+ * direction a is (3 a.Omega.a - 1)/2.  Unit dyads summed in FP32 per
+ * thread, in FP64 across the RVE.
+ *   F      device 9*n_rve (the solve's deformation gradients);
+ *   omega  device 9*n_rve, symmetric 3x3 row-major, trace 1 (zeros for an
+ *          RVE without fibers).
+ * Asynchronous on `stream`, ordered after the batch's previous calls.
+ */
+int rve_orientation(rve_batch* b, const double* F, int32_t precision, double* omega, void* stream);
+
 /* Per-RVE sizes after pruning (HOST arrays of n_rve, any may be NULL). */
 int rve_batch_get_sizes(const rve_batch* b, int32_t* free_nodes, int32_t* active_fibers,
                         int32_t* fixed_fibers);

@@ -14,6 +14,6 @@ from ._lib import (RVE_EADMIT, RVE_ECUDA, RVE_EINVAL, RVE_ENOMEM, RVE_OK, RVE_PR
                    rve_tangent, RVE_NOALLOC_MAX_ACTIVE_FIBERS, RVE_NOALLOC_MAX_FREE_NODES,
                    rve_server_create, rve_server_destroy, rve_server_drain, rve_server_get_stats,
                    rve_server_poll, rve_server_step, rve_server_submit, rve_autotune, rve_batch_get_bins,
-                   rve_set_kernel_timing, rve_last_kernel_ms, rve_tangent_mandel)
+                   rve_set_kernel_timing, rve_last_kernel_ms, rve_tangent_mandel, rve_orientation)
 
 __all__ = [n for n in dir() if n.startswith(("rve_", "RVE_", "Rve"))] + ["lib", "lib_path"]

@@ -53,6 +53,7 @@ rve_solve_plain_noalloc = _sig("rve_solve_plain_noalloc", C.c_int, [_P, _I64, _P
 RVE_NOALLOC_MAX_ACTIVE_FIBERS, RVE_NOALLOC_MAX_FREE_NODES = 16384, 8192
 rve_tangent = _sig("rve_tangent", C.c_int, [_P, _P, _D, _D, _I32, _P, _P, _P, _P])
 rve_tangent_mandel = _sig("rve_tangent_mandel", C.c_int, [_P, _P, _D, _D, _I32, _P, _P, _P, _P])
+rve_orientation = _sig("rve_orientation", C.c_int, [_P, _P, _I32, _P, _P])
 rve_reset_state = _sig("rve_reset_state", C.c_int, [_P, _P, _I64])
 rve_batch_get_info = _sig("rve_batch_get_info", C.c_int, [_P, C.POINTER(rve_batch_info)])
 rve_batch_get_sizes = _sig("rve_batch_get_sizes", C.c_int, [_P, _P, _P, _P])
@@ -241,6 +242,15 @@ class RveBatch:
         _check(rve_tangent_mandel(self.h, _ptr(F), h, tol, max_iter, _ptr(sigma), _ptr(Cm), _ptr(status),
                                   _stream_handle(stream)), "rve_tangent_mandel")
         return sigma, Cm, status
+
+    def orientation(self, F, precision: int | None = None, stream=None):
+        """Orientation tensors (n, 3, 3) at the state of the last solve in ``precision``;
+        the degree of alignment along a unit direction a is (3 a.Omega.a - 1)/2."""
+        import torch
+        prec = self.opt.precision if precision is None else precision
+        om = torch.empty((self.n_rve, 3, 3), dtype=torch.float64, device=F.device)
+        _check(rve_orientation(self.h, _ptr(F), prec, _ptr(om), _stream_handle(stream)), "rve_orientation")
+        return om
 
     def bins(self, precision: int | None = None) -> list[dict]:
         prec = self.opt.precision if precision is None else precision

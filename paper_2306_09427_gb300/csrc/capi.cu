@@ -438,6 +438,91 @@ __global__ void tan_finish(const double* __restrict__ S, const int32_t* __restri
   }
 }
 
+// Orientation tensor Omega = <n (x) n> of every RVE at the state of its last
+// solve (x = F X + h; h = 0 for an RVE not yet solved in that precision),
+// over the active and the boundary-to-boundary fibers (the fibers kept after
+// pruning); Sec. 4 sends it to the macroscale, Sec. 5's alignment measure is
+// P2(a) = (3 a.Omega.a - 1)/2.  One CTA per RVE; per-thread sums in FP32 of
+// unit dyads, per-warp partials summed in FP64.
+constexpr int ORIENT_THREADS = 128;
+
+__global__ void __launch_bounds__(ORIENT_THREADS) orient_kernel(const RveMeta* __restrict__ meta,
+                                                               const FibD* __restrict__ fa,
+                                                               const uint32_t* __restrict__ fij,
+                                                               const FibD* __restrict__ fb,
+                                                               const double* __restrict__ state,
+                                                               const uint8_t* __restrict__ valid,
+                                                               const double* __restrict__ F, double* __restrict__ omega,
+                                                               int64_t r0) {
+  __shared__ double part[ORIENT_THREADS / 32][6];
+  const int64_t r = r0 + blockIdx.x;
+  const RveMeta M = meta[r];
+  const int tid = threadIdx.x;
+  float f[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) f[k] = float(F[9 * r + k]);
+  const bool warm = state && valid && valid[r];
+  const double* st = warm ? state + 4 * size_t(M.node_off) : nullptr;
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  auto add = [&](float dx, float dy, float dz) {
+    const float inv = 1.0f / (dx * dx + dy * dy + dz * dz);
+    acc[0] += dx * dx * inv;
+    acc[1] += dy * dy * inv;
+    acc[2] += dz * dz * inv;
+    acc[3] += dy * dz * inv;
+    acc[4] += dx * dz * inv;
+    acc[5] += dx * dy * inv;
+  };
+  for (int e = tid; e < M.na; e += ORIENT_THREADS) {
+    const FibD& q = fa[M.fa_off + e];
+    const float X0 = float(q.dx), X1 = float(q.dy), X2 = float(q.dz);
+    float dx = f[0] * X0 + f[1] * X1 + f[2] * X2;
+    float dy = f[3] * X0 + f[4] * X1 + f[5] * X2;
+    float dz = f[6] * X0 + f[7] * X1 + f[8] * X2;
+    if (st) {
+      const uint32_t ij = fij[M.fa_off + e];
+      const uint32_t i = ij & 0xffffu, j = ij >> 16;
+      double hx = 0.0, hy = 0.0, hz = 0.0;
+      if (j < uint32_t(M.nf)) {
+        hx += st[4 * j];
+        hy += st[4 * j + 1];
+        hz += st[4 * j + 2];
+      }
+      if (i < uint32_t(M.nf)) {
+        hx -= st[4 * i];
+        hy -= st[4 * i + 1];
+        hz -= st[4 * i + 2];
+      }
+      dx += float(hx);
+      dy += float(hy);
+      dz += float(hz);
+    }
+    add(dx, dy, dz);
+  }
+  for (int e = tid; e < M.nb; e += ORIENT_THREADS) {
+    const FibD& q = fb[M.fb_off + e];
+    const float X0 = float(q.dx), X1 = float(q.dy), X2 = float(q.dz);
+    add(f[0] * X0 + f[1] * X1 + f[2] * X2, f[3] * X0 + f[4] * X1 + f[5] * X2, f[6] * X0 + f[7] * X1 + f[8] * X2);
+  }
+  const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    float v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) part[warp][k] = double(v);
+  }
+  __syncthreads();
+  if (tid < 9) {
+    const int i = tid / 3, j = tid % 3;
+    const int k = (i == j) ? i : 6 - i - j;  // xx yy zz yz xz xy
+    double t = 0.0;
+    for (int w = 0; w < ORIENT_THREADS / 32; ++w) t += part[w][k];
+    const int cnt = M.na + M.nb;
+    omega[9 * r + tid] = cnt > 0 ? t / double(cnt) : 0.0;
+  }
+}
+
 // Buffers of the perturbed solves (both tangents): F, sigma, iterations and
 // status per direction slot, the slots' warm-start states, and the streamed
 // bins' scratch (laid out for all 18 slots; the six-solve tangent uses 0..5).
@@ -965,6 +1050,29 @@ int rve_last_kernel_ms(rve_batch* b, int32_t max, double* ms) {
     ms[k] = double(t);
   }
   return n;
+}
+
+int rve_orientation(rve_batch* b, const double* F, int32_t precision, double* omega, void* stream) {
+  if (!b) return fail(RVE_EINVAL, "null batch");
+  if (b->n_rve == 0) return RVE_OK;
+  if (!F || !omega) return fail(RVE_EINVAL, "F and omega are required");
+  if (precision != RVE_PREC_PLAIN_F64 && precision != RVE_PREC_MIXED && precision != RVE_PREC_BATCHED_F64)
+    return fail(RVE_EINVAL, "unknown precision");
+  TRY(set_device(b));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TRY(order_after_last(b, s));
+  const PathState& P = precision == RVE_PREC_MIXED ? b->pf : b->pd;
+  const double* state = P.ready ? static_cast<const double*>(P.d_state) : nullptr;
+  const uint8_t* valid = P.ready ? P.d_valid : nullptr;
+  const int64_t n = b->n_rve;
+  for (int64_t r0 = 0; r0 < n; r0 += 65535) {  // grid.x limit of a launch over RVEs
+    const int64_t m = std::min<int64_t>(65535, n - r0);
+    orient_kernel<<<unsigned(m), ORIENT_THREADS, 0, s>>>(b->d_meta, b->d_fa, b->d_fij, b->d_fb, state, valid, F,
+                                                          omega, r0);
+    RVE_CUDA_TRY(cudaGetLastError());
+  }
+  RVE_CUDA_TRY(cudaEventRecord(b->ev_last, s));
+  return RVE_OK;
 }
 
 int rve_tangent_mandel(rve_batch* b, const double* F, double h, double tol, int32_t max_iter, double* sigma,

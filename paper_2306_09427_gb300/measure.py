@@ -3,6 +3,7 @@
     python -m paper_2306_09427_gb300.measure single    # one 6^3 RVE, F = I + 0.1 e1 (x) e1
     python -m paper_2306_09427_gb300.measure uneven    # 4096 RVEs, side 6..16, p 0.5..0.8
     python -m paper_2306_09427_gb300.measure tangent   # 32,000 8^3 RVEs, sigma + dsigma/dF, and the six-solve C
+    python -m paper_2306_09427_gb300.measure orientation  # orientation tensors of 1024 x 10^3 RVEs (HBM-bound)
 
 Each line gives the batched mixed-precision path (one solve of the whole
 batch, CUDA events on a created stream, warm-up excluded, median of the
@@ -55,6 +56,34 @@ def _plain(pk_sub, Fs_sub, tol, device):
     return Fs_sub.shape[0] / dt, it.cpu().numpy()
 
 
+def _orientation(b, Fd, stream, reps, res):
+    """Time rve_orientation after a solve, L2 flushed before each launch;
+    algorithmic bytes: per active fiber its reference chord (24 B) and packed
+    endpoints (4 B), per boundary fiber its chord, per free node its state
+    (24 B), per RVE F and Omega (144 B)."""
+    import torch
+    b.solve(Fd, stream=stream)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=Fd.device)
+    ts = []
+    for k in range(reps + 3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        om = b.orientation(Fd, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= 3:
+            ts.append(e0.elapsed_time(e1) / 1e3)
+    nf, na, nb = b.sizes()
+    bytes_alg = float(28 * na.sum() + 24 * nb.sum() + 24 * nf.sum() + 144 * b.n_rve)
+    t = float(np.median(ts))
+    res.update(orientation_s=t, algorithmic_bytes=bytes_alg, achieved_gbs=bytes_alg / t / 1e9,
+               trace_max_dev=float((om.diagonal(dim1=1, dim2=2).sum(-1) - 1).abs().max()))
+    b.close()
+    return res
+
+
 def run(config: str, reps: int = 5, plain_subset: int = 32, tol: float = 3e-7, autotune: bool = True,
         device: int = 0) -> dict:
     import torch
@@ -65,6 +94,9 @@ def run(config: str, reps: int = 5, plain_subset: int = 32, tol: float = 3e-7, a
         tol_m, tol_d = 1e-8, 1e-8
     elif config == "uneven":
         nets, Fs = rvegen.config_uneven(4096)
+        tol_m = tol_d = tol
+    elif config == "orientation":
+        nets, Fs = rvegen.config_uniform(1024)
         tol_m = tol_d = tol
     elif config == "tangent":
         nets = [rvegen.grid_network(8, 0.6, rvegen.Stream(rvegen.rve_seed(4, r))) for r in range(32000)]
@@ -81,6 +113,8 @@ def run(config: str, reps: int = 5, plain_subset: int = 32, tol: float = 3e-7, a
     Fd = torch.tensor(Fs.reshape(-1, 9), dtype=torch.float64, device=f"cuda:{device}")
     res = {"config": config, "n_rve": n, "create_s": t_create, "precision": "f64 batched" if config == "single"
            else "mixed", "tol_rel_residual": tol_m}
+    if config == "orientation":
+        return _orientation(b, Fd, stream, reps, res)
     if config == "tangent":
         b.solve(Fd, stream=stream)  # base state to warm-start from, as inside a load step
         torch.cuda.synchronize()
@@ -114,7 +148,7 @@ def run(config: str, reps: int = 5, plain_subset: int = 32, tol: float = 3e-7, a
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("config", choices=["single", "uneven", "tangent"])
+    ap.add_argument("config", choices=["single", "uneven", "tangent", "orientation"])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--plain-subset", type=int, default=32)
     ap.add_argument("--no-autotune", action="store_true")
