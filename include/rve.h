@@ -99,6 +99,15 @@ typedef struct rve_batch rve_batch; /* opaque, library owned */
  *               It only adds a condition to the residual test and is skipped
  *               once the residual is below 1e-3 * sigma_tol * R_aff.
  *               <= 0 disables it.  Default 0 (off).
+ *  damping_mode RVE_DAMP_VISCOUS (0): mass-proportional viscous damping as
+ *               set by `damping`.  RVE_DAMP_KINETIC (1): kinetic damping,
+ *               the other family of DR accelerations the paper names
+ *               (Sec. 3.2): no viscous term; the kinetic energy sum m |v|^2
+ *               of every step is tracked, and a step whose kinetic energy
+ *               is below the previous step's went past a peak: it is taken
+ *               back, the velocities are set to zero, and the motion
+ *               restarts with the half step v = f/(2m).  Batched precisions only
+ *               (RVE_EINVAL with RVE_PREC_PLAIN_F64).  Default 0.
  */
 typedef struct rve_options {
   double tol;
@@ -110,8 +119,12 @@ typedef struct rve_options {
   int32_t threads;
   int32_t graphs;
   double sigma_tol;
-  int32_t reserved[4];
+  int32_t damping_mode;
+  int32_t reserved[3];
 } rve_options;
+
+#define RVE_DAMP_VISCOUS 0
+#define RVE_DAMP_KINETIC 1
 
 /* Fill *opt with the defaults above.  Never fails. */
 void rve_options_default(rve_options* opt);

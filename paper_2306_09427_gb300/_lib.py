@@ -15,13 +15,14 @@ lib = C.CDLL(lib_path)
 RVE_OK, RVE_EINVAL, RVE_ENOMEM, RVE_ECUDA, RVE_EADMIT = 0, -1, -2, -3, -4
 RVE_STATUS_CONVERGED, RVE_STATUS_MAX_ITER, RVE_STATUS_NONFINITE, RVE_STATUS_EMPTY = 0, 1, 2, 3
 RVE_PREC_PLAIN_F64, RVE_PREC_MIXED, RVE_PREC_BATCHED_F64 = 0, 1, 2
+RVE_DAMP_VISCOUS, RVE_DAMP_KINETIC = 0, 1
 
 
 class rve_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("check_every", C.c_int32),
                 ("precision", C.c_int32), ("warm_start", C.c_int32), ("damping", C.c_double),
                 ("threads", C.c_int32), ("graphs", C.c_int32), ("sigma_tol", C.c_double),
-                ("reserved", C.c_int32 * 4)]
+                ("damping_mode", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class rve_batch_info(C.Structure):

@@ -67,6 +67,10 @@ int valid_options(const rve_options& o) {
   if (!std::isfinite(o.damping)) return fail(RVE_EINVAL, "damping must be finite");
   if (!std::isfinite(o.sigma_tol)) return fail(RVE_EINVAL, "sigma_tol must be finite");
   if (o.graphs != 0 && o.graphs != 1) return fail(RVE_EINVAL, "graphs must be 0 or 1");
+  if (o.damping_mode != RVE_DAMP_VISCOUS && o.damping_mode != RVE_DAMP_KINETIC)
+    return fail(RVE_EINVAL, "damping_mode must be RVE_DAMP_VISCOUS or RVE_DAMP_KINETIC");
+  if (o.damping_mode == RVE_DAMP_KINETIC && o.precision == RVE_PREC_PLAIN_F64)
+    return fail(RVE_EINVAL, "kinetic damping runs on the batched precisions");
   if (o.threads != 0 && o.threads != 64 && o.threads != 128 && o.threads != 256 && o.threads != 512 &&
       o.threads != 1024)
     return fail(RVE_EINVAL, "threads must be 0, 64, 128, 256, 512 or 1024");
@@ -364,6 +368,7 @@ DrArgs<T> make_args(rve_batch* b, const double* F, double tol, int max_iter, dou
   a.max_iter = max_iter;
   a.check_every = b->opt.check_every;
   a.damping = b->opt.damping;
+  a.kinetic = b->opt.damping_mode == RVE_DAMP_KINETIC ? 1 : 0;
   a.sigma_tol = b->opt.sigma_tol;
   return a;
 }
@@ -734,6 +739,7 @@ void rve_options_default(rve_options* o) {
   o->warm_start = 0;
   o->damping = 0.0;
   o->threads = 0;
+  o->damping_mode = RVE_DAMP_VISCOUS;
 }
 
 const char* rve_last_error(void) { return g_error.c_str(); }

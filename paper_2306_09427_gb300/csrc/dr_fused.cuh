@@ -286,6 +286,8 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
   // decisions of a check, published by thread 0: outcome and damping factors
   __shared__ int sFlag;
   __shared__ T sAB[2];
+  // kinetic damping: per-warp kinetic-energy partials, double-buffered by iteration parity
+  __shared__ T sKE[2][32];
 
   const Work wk = A.work[blockIdx.x];
   const RveMeta M = A.meta[wk.rve];
@@ -445,8 +447,15 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
 
   // ---- dynamic relaxation loop
   const int K = A.check_every;
-  const bool adaptive = !(A.damping > 0.0);
-  double c = adaptive ? DAMP_C0 : A.damping;
+  // kinetic damping: no viscous term (c = 0, so alpha = beta = 1); when the
+  // kinetic energy of a step is below the previous step's, that step went
+  // past a peak: it is taken back and the motion restarts from rest.
+  // Otherwise viscous damping, fixed or adaptive.
+  const bool kinetic = A.kinetic != 0;
+  const bool adaptive = !kinetic && !(A.damping > 0.0);
+  double c = kinetic ? 0.0 : (adaptive ? DAMP_C0 : A.damping);
+  T ke_prev = T(0);      // kinetic energy (sum m |v|^2) of the previous iteration's step
+  bool kin_half = true;  // kinetic damping: the next step starts from rest (half step)
   T alpha = T((2.0 - c) / (2.0 + c)), beta = T(2.0 / (2.0 + c));
   if (tid == 0) {
     sAB[0] = alpha;
@@ -662,30 +671,60 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
         do_rebase = std::is_same<T, float>::value && (n_checks % REBASE_EVERY == 0);
       }
       const bool pre_it = adaptive && (to_check == 0);  // the iteration before a check
+      T b_step = beta;    // beta, or beta / 2 on the first step from rest
+      bool undo = false;  // kinetic damping: take back the step that went past a peak
+      if (kinetic) {
+        if (it > 0) {
+          // the kinetic energy of the step taken last iteration (partials
+          // published before the barrier that ended it)
+          const T* kp = sKE[(it - 1) & 1];
+          T ke = T(0);
+          for (int w = 0; w < NT / 32; ++w) ke += kp[w];
+          if (ke < ke_prev) {
+            undo = true;
+            ke_prev = T(0);
+          } else {
+            ke_prev = ke;
+          }
+        }
+        if (kin_half) b_step = T(0.5) * beta;  // central difference's starting half step v = (dt/2) f/m
+      }
+      T ke_t = T(0);
       // update owned nodes
 #pragma unroll
       for (int q = 0; q < NPT; ++q) {
         const int a = tid + q * NT;
         if (a < nf) {
           const T m = T(MASS_COEF) * fw[q];
-          const T bm = k_div(beta, m);  // fictitious mass: an approximate quotient is enough
-          T nvx = alpha * vx[q] + bm * fx[q];
-          T nvy = alpha * vy[q] + bm * fy[q];
-          T nvz = alpha * vz[q] + bm * fz[q];
-          const T sp2 = nvx * nvx + nvy * nvy + nvz * nvz;
-          const T cp = T(cap[q]);
-          if (sp2 > cp * cp) {
-            const T sc = cp * k_rsqrt(sp2);
-            nvx *= sc;
-            nvy *= sc;
-            nvz *= sc;
+          T nvx, nvy, nvz;
+          if (undo) {
+            // past the kinetic-energy peak: back to the position before the
+            // last step, at rest; no step this iteration (the forces just
+            // gathered belong to the position being left)
+            hx[q] -= vx[q];
+            hy[q] -= vy[q];
+            hz[q] -= vz[q];
+            nvx = nvy = nvz = T(0);
+          } else {
+            const T bm = k_div(b_step, m);  // fictitious mass: an approximate quotient is enough
+            nvx = alpha * vx[q] + bm * fx[q];
+            nvy = alpha * vy[q] + bm * fy[q];
+            nvz = alpha * vz[q] + bm * fz[q];
+            const T sp2 = nvx * nvx + nvy * nvy + nvz * nvz;
+            const T cp = T(cap[q]);
+            if (sp2 > cp * cp) {
+              const T sc = cp * k_rsqrt(sp2);
+              nvx *= sc;
+              nvy *= sc;
+              nvz *= sc;
+            }
+            hx[q] += nvx;
+            hy[q] += nvy;
+            hz[q] += nvz;
           }
           vx[q] = nvx;
           vy[q] = nvy;
           vz[q] = nvz;
-          hx[q] += nvx;
-          hy[q] += nvy;
-          hz[q] += nvz;
           V4 h4;
           h4.x = hx[q];
           h4.y = hy[q];
@@ -696,9 +735,15 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
             pre += nvx * fx[q] + nvy * fy[q] + nvz * fz[q];
             pm += m * (nvx * nvx + nvy * nvy + nvz * nvz);
           }
+          if (kinetic) ke_t += m * (nvx * nvx + nvy * nvy + nvz * nvz);
         }
       }
+      kin_half = undo;  // after a take-back the next step starts from rest
       if (pre_it) have_pre = true;
+      if (kinetic) {
+        ke_t = warp_sum_t(ke_t);
+        if ((tid & 31) == 0) sKE[it & 1][tid >> 5] = ke_t;
+      }
       if (do_rebase) {
         rebase<T, NT, NPT>(A, wk, M, sF, H, P0, P1, HR, false, true, hx, hy, hz);
       } else {

@@ -142,6 +142,7 @@ struct DrArgs {
   int32_t check_every;
   double damping;          // > 0 fixed, <= 0 adaptive
   double sigma_tol;        // > 0: also require the estimated stress error <= sigma_tol
+  int32_t kinetic;         // 1: kinetic damping (no viscous term, velocity reset after a kinetic-energy peak)
 };
 
 }  // namespace rvegpu
