@@ -22,8 +22,14 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
-int launch_bin(const DrArgs<float>& a, const Bin& bin, cudaStream_t s);
-int launch_bin(const DrArgs<double>& a, const Bin& bin, cudaStream_t s);
+int launch_bin_viscous(const DrArgs<float>& a, const Bin& bin, cudaStream_t s);
+int launch_bin_viscous(const DrArgs<double>& a, const Bin& bin, cudaStream_t s);
+int launch_bin_kinetic(const DrArgs<float>& a, const Bin& bin, cudaStream_t s);
+int launch_bin_kinetic(const DrArgs<double>& a, const Bin& bin, cudaStream_t s);
+template <typename T>
+int launch_bin(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
+  return a.kinetic ? launch_bin_kinetic(a, bin, s) : launch_bin_viscous(a, bin, s);
+}
 int plain_scratch_bytes(int nf_max, int na_max);
 int plain_solve_one(rve_batch* b, int r, int out, const double* F, double tol, int max_iter, double* sigma,
                     int32_t* iters, int32_t* status, cudaStream_t s);

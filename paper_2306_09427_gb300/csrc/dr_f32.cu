@@ -1,6 +1,8 @@
-// Fused batched kernel, mixed precision (FP32 forces/updates, FP64 sums).
+// Fused batched kernel, mixed precision (FP32 forces/updates, FP64 sums), viscous damping.
 #include "dr_launch.cuh"
 
 namespace rvegpu {
-int launch_bin(const DrArgs<float>& a, const Bin& bin, cudaStream_t s) { return launch_bin_t<float>(a, bin, s); }
+int launch_bin_viscous(const DrArgs<float>& a, const Bin& bin, cudaStream_t s) {
+  return launch_bin_t<float, false>(a, bin, s);
+}
 }  // namespace rvegpu

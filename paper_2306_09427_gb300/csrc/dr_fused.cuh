@@ -274,7 +274,9 @@ __device__ __forceinline__ void rebase(const DrArgs<T>& A, const Work& wk, const
   __syncthreads();
 }
 
-template <typename T, int NT, int NPT, int MODE>
+// KIN: kinetic damping (a separate instantiation, so that the viscous
+// default carries none of its code or registers).
+template <typename T, int NT, int NPT, int MODE, bool KIN>
 __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const DrArgs<T> A) {
   using V4 = typename Vec4<T>::t;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
   // kinetic energy of a step is below the previous step's, that step went
   // past a peak: it is taken back and the motion restarts from rest.
   // Otherwise viscous damping, fixed or adaptive.
-  const bool kinetic = A.kinetic != 0;
+  constexpr bool kinetic = KIN;
   const bool adaptive = !kinetic && !(A.damping > 0.0);
   double c = kinetic ? 0.0 : (adaptive ? DAMP_C0 : A.damping);
   T ke_prev = T(0);      // kinetic energy (sum m |v|^2) of the previous iteration's step
