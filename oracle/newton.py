@@ -173,12 +173,17 @@ def _newton(pb, x, tol_abs, max_iter):
 
 
 def _lowest_mode(K):
+    """A direction of lowest curvature for the saddle escape.  Exact for small
+    K; otherwise a bounded Lanczos search: on sub-isostatic networks K has a
+    large cluster of near-zero eigenvalues (floppy modes), no single lowest
+    mode converges in reasonable time, and any direction of the cluster's
+    best Ritz vector (or a fixed direction) serves the escape step."""
     n = K.shape[0]
     if n <= 3000:
         w, V = np.linalg.eigh(K.toarray())
         return w[0], V[:, 0]
     try:
-        w, V = sla.eigsh(K, k=1, which="SA", tol=1e-6, maxiter=50 * n)
+        w, V = sla.eigsh(K, k=1, which="SA", tol=1e-6, maxiter=300)
         return w[0], V[:, 0]
     except sla.ArpackNoConvergence as err:  # take the best Ritz vector, else a fixed direction
         if err.eigenvectors is not None and err.eigenvectors.shape[1] > 0:
