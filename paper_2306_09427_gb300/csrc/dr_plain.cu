@@ -479,7 +479,7 @@ int plain_run(rve_batch* b, int r, int out, const double* F, double tol, int max
         if (adaptive && have_pre && pm > 0.0) {
           const double lam = -(post - pre) / pm;
           if (lam > 0.0) {
-            c = std::fmin(2.0 * std::sqrt(lam), DAMP_C_MAX);
+            c = std::fmin(DAMP_SCALE * 2.0 * std::sqrt(lam), DAMP_C_MAX);
             alpha = (2.0 - c) / (2.0 + c);
             beta = 2.0 / (2.0 + c);
           }

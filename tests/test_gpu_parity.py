@@ -8,6 +8,8 @@ Bars (sigma, relative Frobenius error against the oracle):
 import json
 import os
 
+import time
+
 import numpy as np
 import pytest
 
@@ -222,8 +224,10 @@ def test_uneven_batch(rve):
     for prec, kw, bound in ((rve.RVE_PREC_MIXED, {}, 1e-4),
                             (rve.RVE_PREC_BATCHED_F64, dict(tol=1e-10, sigma_tol=0.0, max_iter=2_000_000), 1e-6)):
         b = rve.RveBatch(rvegen.pack(nets), precision=prec, **kw)
+        t0 = time.perf_counter()
         s, it, st = b.solve(_F(Fs))
-        s, st = s.cpu().numpy().reshape(-1, 3, 3), st.cpu().numpy()
+        s, st, it = s.cpu().numpy().reshape(-1, 3, 3), st.cpu().numpy(), it.cpu().numpy()
+        t1 = time.perf_counter()
         kinds = []
         for r in rows:
             if not r["converged"]:
@@ -232,7 +236,8 @@ def test_uneven_batch(rve):
             assert st[k] == rve.RVE_STATUS_CONVERGED, (prec, k)
             kinds.append(match_or_other_minimum(b, k, nets[k], Fs[k], s[k], prec, bound,
                                                 np.array(r["sigma"]).reshape(3, 3)))
-        print("uneven precision", prec, {k: kinds.count(k) for k in set(kinds)})
+        print("uneven precision", prec, {k: kinds.count(k) for k in set(kinds)},
+              "solve %.1f s (max %d iterations), oracle checks %.1f s" % (t1 - t0, it.max(), time.perf_counter() - t1))
         assert kinds.count("other") <= len(kinds) // 2
         b.close()
 
