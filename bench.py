@@ -42,7 +42,7 @@ FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused-kernel launch on
 # this workload (ncu capture summarised in profiles/dr_fused_uniform1024_full.md);
 # None whenever the kernel changes after that capture
-TRAFFIC_BYTES_PER_LAUNCH = 105.43e6 + 5.84e6
+TRAFFIC_BYTES_PER_LAUNCH = 105.95e6 + 5.87e6
 
 
 def _config():
