@@ -32,6 +32,7 @@ N_RVE = 1024
 SIDE = 10
 TOL = 3e-7          # relative residual of the mixed path (library default; sigma err <= 1e-4 validated)
 SIGMA_TOL = 0.0     # stress-convergence criterion off (library default)
+DAMPING_SCALE = 0.7  # c = 0.7 * 2 sqrt(lambda_RQ) on both paths timed (parity-tested at this setting)
 PLAIN_SUBSET = 32   # RVEs timed on the plain FP64 per-RVE path
 # algorithmic FP32 work per fiber-update (FMA = 2 flops): fiber force 39
 # (chord update 3, Green strain 13, length 6, law 4, stiffness bound 7,
@@ -42,13 +43,14 @@ FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused-kernel launch on
 # this workload (ncu capture summarised in profiles/dr_fused_uniform1024_full.md);
 # None whenever the kernel changes after that capture
-TRAFFIC_BYTES_PER_LAUNCH = 105.95e6 + 5.87e6
+TRAFFIC_BYTES_PER_LAUNCH = 105.62e6 + 5.48e6
 
 
 def _config():
     return {"workload": "uniform batch: 1024 RVEs, 10x10x10 jittered grid, bond p=0.6, EA=1, B=10, "
                         "random F=R.U (principal strains U[-0.05,0.15])",
-            "n_rve": N_RVE, "grid_side": SIDE, "tol_rel_residual": TOL, "sigma_tol": SIGMA_TOL, "precision": "mixed (FP32 forces/updates, "
+            "n_rve": N_RVE, "grid_side": SIDE, "tol_rel_residual": TOL, "sigma_tol": SIGMA_TOL,
+            "damping_scale": DAMPING_SCALE, "precision": "mixed (FP32 forces/updates, "
             "FP64 residual and stress sums)", "start": "cold (h=0) every step", "l2": "flushed between timed steps "
             "(256 MiB write)"}
 
@@ -181,7 +183,8 @@ def run_ours(args, rank, world, local):
     # each rank solves its own shard of independent RVEs (weak scaling)
     nets, Fs = rvegen.config_uniform(N_RVE, side=SIDE, first=rank * N_RVE)
     pk = rvegen.pack(nets)
-    b = rve.RveBatch(pk, device=local, precision=rve.RVE_PREC_MIXED, tol=TOL, sigma_tol=SIGMA_TOL, warm_start=0)
+    b = rve.RveBatch(pk, device=local, precision=rve.RVE_PREC_MIXED, tol=TOL, sigma_tol=SIGMA_TOL, warm_start=0,
+                     damping_scale=DAMPING_SCALE)
     Fd = torch.tensor(Fs.reshape(-1, 9), dtype=torch.float64, device=dev)
     sigma = torch.empty((N_RVE, 9), dtype=torch.float64, device=dev)
     iters = torch.empty(N_RVE, dtype=torch.int32, device=dev)
@@ -253,7 +256,8 @@ def run_ours(args, rank, world, local):
     plain = None
     if rank == 0 and not args.no_plain:
         sub = rvegen.pack(nets[:PLAIN_SUBSET])
-        bp = rve.RveBatch(sub, device=local, precision=rve.RVE_PREC_PLAIN_F64, tol=TOL, sigma_tol=SIGMA_TOL)
+        bp = rve.RveBatch(sub, device=local, precision=rve.RVE_PREC_PLAIN_F64, tol=TOL, sigma_tol=SIGMA_TOL,
+                          damping_scale=DAMPING_SCALE)
         sp = torch.empty((PLAIN_SUBSET, 9), dtype=torch.float64, device=dev)
         bp.solve(Fd[:PLAIN_SUBSET].contiguous(), sigma=sp)
         torch.cuda.synchronize()

@@ -108,6 +108,13 @@ typedef struct rve_batch rve_batch; /* opaque, library owned */
  *               back, the velocities are set to zero, and the motion
  *               restarts with the half step v = f/(2m).  Batched precisions only
  *               (RVE_EINVAL with RVE_PREC_PLAIN_F64).  Default 0.
+ *  damping_scale  s in the adaptive damping c = s * 2 sqrt(lambda) (lambda
+ *               the Rayleigh quotient of the last step's velocity, which
+ *               sits above the slowest mode's eigenvalue).  Default 1.0;
+ *               0.7 takes about 20 % fewer iterations on the uniform and
+ *               uneven workloads, but one 16^3 network solved in FP64 to
+ *               1e-10 with it stopped on a weakly unstable equilibrium.
+ *               Must be in (0, 1]; 0 means the default.
  */
 typedef struct rve_options {
   double tol;
@@ -120,7 +127,8 @@ typedef struct rve_options {
   int32_t graphs;
   double sigma_tol;
   int32_t damping_mode;
-  int32_t reserved[3];
+  int32_t reserved0;
+  double damping_scale;
 } rve_options;
 
 #define RVE_DAMP_VISCOUS 0

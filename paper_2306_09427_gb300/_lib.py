@@ -22,7 +22,7 @@ class rve_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("check_every", C.c_int32),
                 ("precision", C.c_int32), ("warm_start", C.c_int32), ("damping", C.c_double),
                 ("threads", C.c_int32), ("graphs", C.c_int32), ("sigma_tol", C.c_double),
-                ("damping_mode", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("damping_mode", C.c_int32), ("reserved0", C.c_int32), ("damping_scale", C.c_double)]
 
 
 class rve_batch_info(C.Structure):

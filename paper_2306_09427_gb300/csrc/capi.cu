@@ -73,6 +73,8 @@ int valid_options(const rve_options& o) {
   if (!std::isfinite(o.damping)) return fail(RVE_EINVAL, "damping must be finite");
   if (!std::isfinite(o.sigma_tol)) return fail(RVE_EINVAL, "sigma_tol must be finite");
   if (o.graphs != 0 && o.graphs != 1) return fail(RVE_EINVAL, "graphs must be 0 or 1");
+  if (!(o.damping_scale >= 0.0 && o.damping_scale <= 1.0))
+    return fail(RVE_EINVAL, "damping_scale must be in (0, 1] (0 = default)");
   if (o.damping_mode != RVE_DAMP_VISCOUS && o.damping_mode != RVE_DAMP_KINETIC)
     return fail(RVE_EINVAL, "damping_mode must be RVE_DAMP_VISCOUS or RVE_DAMP_KINETIC");
   if (o.damping_mode == RVE_DAMP_KINETIC && o.precision == RVE_PREC_PLAIN_F64)
@@ -375,6 +377,7 @@ DrArgs<T> make_args(rve_batch* b, const double* F, double tol, int max_iter, dou
   a.check_every = b->opt.check_every;
   a.damping = b->opt.damping;
   a.kinetic = b->opt.damping_mode == RVE_DAMP_KINETIC ? 1 : 0;
+  a.damping_scale = b->opt.damping_scale > 0.0 ? b->opt.damping_scale : DAMP_SCALE;
   a.sigma_tol = b->opt.sigma_tol;
   return a;
 }
@@ -746,6 +749,7 @@ void rve_options_default(rve_options* o) {
   o->damping = 0.0;
   o->threads = 0;
   o->damping_mode = RVE_DAMP_VISCOUS;
+  o->damping_scale = DAMP_SCALE;
 }
 
 const char* rve_last_error(void) { return g_error.c_str(); }

@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
               } else if (adaptive && have_pre && v3[2] > 0.0) {
                 const double lam = -v3[1] / v3[2];
                 if (lam > 0.0) {
-                  c = fmin(DAMP_SCALE * 2.0 * sqrt(lam), DAMP_C_MAX);
+                  c = fmin(A.damping_scale * 2.0 * sqrt(lam), DAMP_C_MAX);
                   sAB[0] = T((2.0 - c) / (2.0 + c));
                   sAB[1] = T(2.0 / (2.0 + c));
                 }

@@ -423,6 +423,7 @@ int plain_run(rve_batch* b, int r, int out, const double* F, double tol, int max
   const int K = b->opt.check_every;
   const bool adaptive = !(b->opt.damping > 0.0);
   double c = adaptive ? DAMP_C0 : b->opt.damping;
+  const double scale = b->opt.damping_scale > 0.0 ? b->opt.damping_scale : DAMP_SCALE;
   double alpha = (2.0 - c) / (2.0 + c), beta = 2.0 / (2.0 + c);
   bool have_pre = false;
   double sig_hist[SIG_WINDOW + 1][8] = {};  // ring of (stress, residual, present) per check
@@ -479,7 +480,7 @@ int plain_run(rve_batch* b, int r, int out, const double* F, double tol, int max
         if (adaptive && have_pre && pm > 0.0) {
           const double lam = -(post - pre) / pm;
           if (lam > 0.0) {
-            c = std::fmin(DAMP_SCALE * 2.0 * std::sqrt(lam), DAMP_C_MAX);
+            c = std::fmin(scale * 2.0 * std::sqrt(lam), DAMP_C_MAX);
             alpha = (2.0 - c) / (2.0 + c);
             beta = 2.0 / (2.0 + c);
           }

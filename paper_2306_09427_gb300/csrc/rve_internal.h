@@ -65,10 +65,11 @@ struct Work {
 //                 lambda the Rayleigh quotient v.K v / v.M v of the last
 //                 step's velocity: critical damping of a mode with that
 //                 eigenvalue.  The quotient sits above the slowest mode's
-//                 eigenvalue, and DAMP_SCALE = 0.7 takes about 20 % fewer
+//                 eigenvalue, and a scale of 0.7 takes about 20 % fewer
 //                 iterations, but with it one 16^3 uneven RVE solved in FP64
 //                 to 1e-10 stopped on a weakly unstable equilibrium that the
-//                 oracle could not certify stable; 1.0 is kept.
+//                 oracle could not certify stable; the default DAMP_SCALE is
+//                 1.0 and the option damping_scale sets another.
 constexpr double MASS_GAMMA = 1.1;
 constexpr double MASS_COEF = MASS_GAMMA * 0.25 * 2.0;
 constexpr double STEP_CAP = 0.1;
@@ -150,6 +151,7 @@ struct DrArgs {
   double damping;          // > 0 fixed, <= 0 adaptive
   double sigma_tol;        // > 0: also require the estimated stress error <= sigma_tol
   int32_t kinetic;         // 1: kinetic damping (no viscous term, velocity reset after a kinetic-energy peak)
+  double damping_scale;    // s in the adaptive damping c = s * 2 sqrt(lambda)
 };
 
 }  // namespace rvegpu

@@ -73,7 +73,8 @@ def test_malformed_inputs_rejected_on_host(rve, mutate, msg):
 
 def test_bad_options_rejected(rve):
     for kw in (dict(tol=0.0), dict(check_every=0), dict(precision=7), dict(threads=100), dict(warm_start=3),
-               dict(damping_mode=2), dict(damping_mode=1, precision=0)):
+               dict(damping_mode=2), dict(damping_mode=1, precision=0), dict(damping_scale=1.5),
+               dict(damping_scale=-0.1)):
         with pytest.raises(rve.RveError) as e:
             rve.RveBatch(_packed(), **kw)
         assert e.value.code == rve.RVE_EINVAL

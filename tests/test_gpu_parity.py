@@ -167,12 +167,17 @@ def test_kinetic_damping_converges_to_same_state(rve, small_case, precision, tol
 
 # --------------------------------------- full-size uniform batch (1024 x 10^3)
 
-def test_uniform_full_batch_sampled(rve):
-    """The bench's workload and launch configuration (default options)."""
+BENCH_OPTS = dict(damping_scale=0.7)  # bench.py's options beyond the library defaults
+
+
+@pytest.mark.parametrize("opts", [{}, BENCH_OPTS], ids=["defaults", "bench"])
+def test_uniform_full_batch_sampled(rve, opts):
+    """The bench's workload, with the library defaults and in the launch
+    configuration bench.py times."""
     import torch
     rows = _golden("uniform_10")
     nets, Fs = rvegen.config_uniform(1024)
-    b = rve.RveBatch(rvegen.pack(nets), precision=rve.RVE_PREC_MIXED)
+    b = rve.RveBatch(rvegen.pack(nets), precision=rve.RVE_PREC_MIXED, **opts)
     s, it, st = b.solve(_F(Fs))
     s, st = s.cpu().numpy().reshape(-1, 3, 3), st.cpu().numpy()
     assert (st == rve.RVE_STATUS_CONVERGED).all()
@@ -188,7 +193,7 @@ def test_uniform_full_batch_sampled(rve):
     assert np.isfinite(s).all()
     assert np.abs(s - s.transpose(0, 2, 1)).max() <= 1e-12 * np.abs(s).max()
     # every RVE against a tight FP64 solve of the same DR (same start, same rule)
-    b64 = rve.RveBatch(rvegen.pack(nets), precision=rve.RVE_PREC_BATCHED_F64, tol=1e-10, sigma_tol=0.0)
+    b64 = rve.RveBatch(rvegen.pack(nets), precision=rve.RVE_PREC_BATCHED_F64, tol=1e-10, sigma_tol=0.0, **opts)
     s64, _, _ = b64.solve(_F(Fs))
     s64 = s64.cpu().numpy().reshape(-1, 3, 3)
     e = np.linalg.norm((s - s64).reshape(1024, -1), axis=1) / np.linalg.norm(s64.reshape(1024, -1), axis=1)
@@ -221,7 +226,7 @@ def test_uneven_batch(rve):
     rows = _golden("uneven")
     n = max(r["index"] for r in rows) + 1
     nets, Fs = rvegen.config_uneven(n)
-    for prec, kw, bound in ((rve.RVE_PREC_MIXED, {}, 1e-4),
+    for prec, kw, bound in ((rve.RVE_PREC_MIXED, {}, 1e-4), (rve.RVE_PREC_MIXED, BENCH_OPTS, 1e-4),
                             (rve.RVE_PREC_BATCHED_F64, dict(tol=1e-10, sigma_tol=0.0, max_iter=2_000_000), 1e-6)):
         b = rve.RveBatch(rvegen.pack(nets), precision=prec, **kw)
         t0 = time.perf_counter()
@@ -236,7 +241,7 @@ def test_uneven_batch(rve):
             assert st[k] == rve.RVE_STATUS_CONVERGED, (prec, k)
             kinds.append(match_or_other_minimum(b, k, nets[k], Fs[k], s[k], prec, bound,
                                                 np.array(r["sigma"]).reshape(3, 3)))
-        print("uneven precision", prec, {k: kinds.count(k) for k in set(kinds)},
+        print("uneven precision", prec, kw, {k: kinds.count(k) for k in set(kinds)},
               "solve %.1f s (max %d iterations), oracle checks %.1f s" % (t1 - t0, it.max(), time.perf_counter() - t1))
         assert kinds.count("other") <= len(kinds) // 2
         b.close()
