@@ -116,11 +116,20 @@ def _stream_handle(stream) -> int | None:
     return getattr(stream, "cuda_stream", stream)
 
 
+_OPTION_NAMES = frozenset(n for n, _ in rve_options._fields_ if not n.startswith("reserved"))
+
+
+def _set_fields(o: rve_options, kw: dict) -> None:
+    for k, v in kw.items():
+        if k not in _OPTION_NAMES:  # a ctypes structure would silently take a new attribute
+            raise TypeError(f"unknown option {k!r}; options are {sorted(_OPTION_NAMES)}")
+        setattr(o, k, v)
+
+
 def options(**kw) -> rve_options:
     o = rve_options()
     rve_options_default(C.byref(o))
-    for k, v in kw.items():
-        setattr(o, k, v)
+    _set_fields(o, kw)
     return o
 
 
@@ -155,8 +164,7 @@ class RveBatch:
             pass
 
     def set_options(self, **kw) -> None:
-        for k, v in kw.items():
-            setattr(self.opt, k, v)
+        _set_fields(self.opt, kw)
         _check(rve_set_options(self.h, C.byref(self.opt)), "rve_set_options")
 
     def info(self) -> dict:

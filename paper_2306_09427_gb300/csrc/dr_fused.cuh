@@ -17,11 +17,16 @@
 //            a fixed CSR order, four entries per 8-byte load (runs padded
 //            with a zero slot); deterministic, no atomics (the paper's
 //            getInternalForces scatters with atomics, Sec. 4.3);
-//     check  every check_every iterations: ||f_free||_2 in FP64 against
-//            max(tol R_aff, 1e-16 sum EA) and, with sigma_tol > 0, the
-//            estimated remaining stress error; damping re-estimated;
+//     check  every check_every iterations: ||f_free||_2 (per-thread and
+//            per-warp partials in T, summed across warps in FP64 by warp 0)
+//            against max(tol R_aff, 1e-16 sum EA) and, with sigma_tol > 0,
+//            the estimated remaining stress error; damping re-estimated,
+//            c = s 2 sqrt(lambda) from the Rayleigh quotient lambda; thread 0
+//            takes these block-uniform decisions and publishes them;
 //     update m = MASS_COEF sbar_sum, v <- ((2-c) v + 2 f/m)/(2+c),
-//            |v| capped, h <- h + v (dt = 1).
+//            |v| capped, h <- h + v (dt = 1); with KIN (kinetic damping)
+//            c = 0 and a step past a kinetic-energy peak is taken back and
+//            the motion restarts from rest.
 //   finish   sigma = (sigma_bb + sum_e s_e d_e (x) d_e) / (det F V0) with
 //            FP64 compensated (TwoSum) accumulation; h saved for warm starts.
 //

@@ -71,6 +71,11 @@ def test_malformed_inputs_rejected_on_host(rve, mutate, msg):
     assert msg in str(e.value)
 
 
+def test_unknown_option_name_rejected(rve):
+    with pytest.raises(TypeError):
+        rve.RveBatch(_packed(), damping_scal=0.7)
+
+
 def test_bad_options_rejected(rve):
     for kw in (dict(tol=0.0), dict(check_every=0), dict(precision=7), dict(threads=100), dict(warm_start=3),
                dict(damping_mode=2), dict(damping_mode=1, precision=0), dict(damping_scale=1.5),
