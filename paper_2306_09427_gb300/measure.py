@@ -42,9 +42,9 @@ def _time_solves(b, Fd, reps, stream, tangent=False):
     return float(np.median(out)), res
 
 
-def _plain(pk_sub, Fs_sub, tol, device):
+def _plain(pk_sub, Fs_sub, tol, device, damping_scale=1.0):
     import torch
-    b = RveBatch(pk_sub, device=device, precision=RVE_PREC_PLAIN_F64, tol=tol)
+    b = RveBatch(pk_sub, device=device, precision=RVE_PREC_PLAIN_F64, tol=tol, damping_scale=damping_scale)
     Fd = torch.tensor(Fs_sub.reshape(-1, 9), dtype=torch.float64, device=f"cuda:{device}")
     b.solve(Fd)
     torch.cuda.synchronize()
@@ -85,7 +85,7 @@ def _orientation(b, Fd, stream, reps, res):
 
 
 def run(config: str, reps: int = 5, plain_subset: int = 32, tol: float = 3e-7, autotune: bool = True,
-        device: int = 0) -> dict:
+        device: int = 0, damping_scale: float = 1.0) -> dict:
     import torch
     torch.cuda.set_device(device)
     stream = torch.cuda.Stream()
@@ -108,11 +108,12 @@ def run(config: str, reps: int = 5, plain_subset: int = 32, tol: float = 3e-7, a
     pk = rvegen.pack(nets)
     n = len(nets)
     prec = RVE_PREC_BATCHED_F64 if config == "single" else RVE_PREC_MIXED
-    b = RveBatch(pk, device=device, precision=prec, tol=tol_m, graphs=1, warm_start=int(config == "tangent"))
+    b = RveBatch(pk, device=device, precision=prec, tol=tol_m, graphs=1, warm_start=int(config == "tangent"),
+                 damping_scale=damping_scale)
     t_create = time.perf_counter() - t0
     Fd = torch.tensor(Fs.reshape(-1, 9), dtype=torch.float64, device=f"cuda:{device}")
     res = {"config": config, "n_rve": n, "create_s": t_create, "precision": "f64 batched" if config == "single"
-           else "mixed", "tol_rel_residual": tol_m}
+           else "mixed", "tol_rel_residual": tol_m, "damping_scale": damping_scale}
     if config == "orientation":
         return _orientation(b, Fd, stream, reps, res)
     if config == "tangent":
@@ -136,7 +137,7 @@ def run(config: str, reps: int = 5, plain_subset: int = 32, tol: float = 3e-7, a
                    converged_frac=float((st.cpu().numpy() == 0).mean()), bins=b.bins())
     m = min(plain_subset, n)
     sub = rvegen.pack(nets[:m])
-    pv, pit = _plain(sub, Fs[:m], tol_d, device)
+    pv, pit = _plain(sub, Fs[:m], tol_d, device, damping_scale)
     # the plain path solves from the affine start; for the tangent the batched
     # solves are warm-started, so the ratio there compares unlike solves
     res.update(plain_fp64_subset=m, plain_fp64_solves_per_s=pv, plain_iters_mean=float(pit.mean()),
@@ -152,8 +153,10 @@ def main():
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--plain-subset", type=int, default=32)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--damping-scale", type=float, default=1.0, help="s in c = s * 2 sqrt(lambda), both paths")
     a = ap.parse_args()
-    print(json.dumps(run(a.config, a.reps, a.plain_subset, autotune=not a.no_autotune)))
+    print(json.dumps(run(a.config, a.reps, a.plain_subset, autotune=not a.no_autotune,
+                         damping_scale=a.damping_scale)))
 
 
 if __name__ == "__main__":
