@@ -169,6 +169,24 @@ def oracle_baseline(budget_s: float = 20.0, tol: float = 1e-6):
 
 # -------------------------------------------------------------------- GPU
 
+def serving_latency(device: int, pool: int = 2000, rate: float = 20000.0, duration: float = 3.0) -> dict:
+    """p50/p99 request latency through the continuous-batching server (outside
+    the timed region): a Poisson stream of single RVE solves, each request an
+    RVE of a resident pool (sides 6, 8, 12, 16) under its own F, library
+    defaults, warm starts kept on the device."""
+    import rvegen
+    import paper_2306_09427_gb300 as rve
+    from paper_2306_09427_gb300.serve import pool_networks, request_stream, run_poisson
+    b = rve.RveBatch(rvegen.pack(pool_networks(pool)), device=device, precision=rve.RVE_PREC_MIXED, warm_start=1)
+    t, ids, F = request_stream(pool, rate, duration)
+    r = run_poisson(b, t, ids, F)
+    b.close()
+    return {"p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "throughput": r["throughput"], "unit": "requests/s",
+            "offered_rate": r["offered_rate"], "requests": r["requests"], "converged_frac": r["converged_frac"],
+            "workload": f"Poisson stream {rate:.0f}/s for {duration:.0f} s over a pool of {pool} RVEs "
+                        "(sides 6, 8, 12, 16), warm starts resident"}
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -290,6 +308,8 @@ def run_ours(args, rank, world, local):
         "speedup_vs_plain": (value / world) / plain if plain else None,
         "batch": info,
     }
+    if rank == 0 and not args.no_serve:
+        res["latency"] = serving_latency(local)
     if rank == 0 and not args.no_cpu:
         res["cpu_baseline"] = oracle_baseline(args.cpu_budget)
     if world > 1:
@@ -333,6 +353,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for the CPU baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-latency measurement")
     args = ap.parse_args()
     rank, world, local = _dist()
     if args.impl == "reference":
