@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -190,12 +191,16 @@ int launch_sorted(rve_batch* b, const Bin& bin, cudaStream_t s, const int32_t* l
   int n2 = 1;
   while (n2 < bin.n) n2 <<= 1;
   static bool attr_set[64] = {};
+  static std::mutex attr_mu;
   int dev = 0;
   RVE_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 64 && !attr_set[dev]) {
-    RVE_CUDA_TRY(cudaFuncSetAttribute(lpt_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      int(LPT_MAX * sizeof(unsigned long long))));
-    attr_set[dev] = true;
+  {
+    std::lock_guard<std::mutex> lock(attr_mu);
+    if (dev >= 64 || !attr_set[dev]) {
+      RVE_CUDA_TRY(cudaFuncSetAttribute(lpt_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        int(LPT_MAX * sizeof(unsigned long long))));
+      if (dev < 64) attr_set[dev] = true;
+    }
   }
   lpt_sort<<<1, 1024, size_t(n2) * sizeof(unsigned long long), s>>>(bin.d_work, bin.d_sorted, bin.n, b->d_meta,
                                                                      last_iters);

@@ -1,6 +1,8 @@
 // Instantiation and launch of the fused kernel for one bin.
 #pragma once
 
+#include <mutex>
+
 #include "batch.h"
 #include "dr_fused.cuh"
 
@@ -9,12 +11,19 @@ namespace rvegpu {
 template <typename T, int NT, int NPT, int MODE, bool KIN>
 int launch_variant(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
   auto fn = dr_fused_kernel<T, NT, NPT, MODE, KIN>;
-  static int smem_set[64] = {};  // per device ordinal
+  // largest dynamic shared memory opted in so far, per device ordinal; the
+  // check and the attribute call stay together under one lock, so no thread
+  // launches on a size another thread has recorded but not yet set
+  static int smem_set[64] = {};
+  static std::mutex smem_mu;
   int dev = 0;
   RVE_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 64 && smem_set[dev] < int(bin.smem)) {
-    RVE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bin.smem)));
-    smem_set[dev] = int(bin.smem);
+  {
+    std::lock_guard<std::mutex> lock(smem_mu);
+    if (dev >= 64 || smem_set[dev] < int(bin.smem)) {
+      RVE_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bin.smem)));
+      if (dev < 64) smem_set[dev] = int(bin.smem);
+    }
   }
   DrArgs<T> b = a;
   b.work = bin.d_work;
