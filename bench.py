@@ -84,7 +84,6 @@ class ClockSampler:
             self.p = None
 
     def stop(self, t0: float = 0.0, t1: float = float("inf")):
-        import datetime
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
@@ -93,6 +92,13 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.p.kill()
             out, _ = self.p.communicate()
+        return self.summarise(out, t0, t1)
+
+    @staticmethod
+    def summarise(out: str, t0: float = 0.0, t1: float = float("inf")) -> dict:
+        """Median SM clock under load, maximum clock and active throttle reasons
+        of the csv lines (query Q) whose timestamps fall in [t0, t1]."""
+        import datetime
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
