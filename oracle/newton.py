@@ -145,9 +145,10 @@ def _newton(pb, x, tol_abs, max_iter):
         p = lu.solve(r)
         pred = float(r @ p) - 0.5 * float(p @ (K @ p))
         xt = pb.place(x, x[pb.free_ids].ravel() + p)
-        Wt = pb.energy(xt)
-        rt = pb.residual(xt)
-        rtn = float(np.linalg.norm(rt))
+        with np.errstate(over="ignore", invalid="ignore"):  # a wild trial step is rejected below
+            Wt = pb.energy(xt)
+            rt = pb.residual(xt)
+            rtn = float(np.linalg.norm(rt))
         if pred > 1e-12 * max(abs(W0), 1e-300):
             rho = (W0 - Wt) / pred
             accept = rho > 1e-4 and np.isfinite(rtn)
