@@ -4,6 +4,7 @@
     python -m paper_2306_09427_gb300.measure uneven    # 4096 RVEs, side 6..16, p 0.5..0.8
     python -m paper_2306_09427_gb300.measure tangent   # 32,000 8^3 RVEs, sigma + dsigma/dF, and the six-solve C
     python -m paper_2306_09427_gb300.measure orientation  # orientation tensors of 1024 x 10^3 RVEs (HBM-bound)
+    python -m paper_2306_09427_gb300.measure streamed  # 152 RVEs of side 15-16 (streamed kernel variants)
 
 Each line gives the batched mixed-precision path (one solve of the whole
 batch, CUDA events on a created stream, warm-up excluded, median of the
@@ -95,6 +96,10 @@ def run(config: str, reps: int = 5, plain_subset: int = 32, tol: float = 3e-7, a
     elif config == "uneven":
         nets, Fs = rvegen.config_uneven(4096)
         tol_m = tol_d = tol
+    elif config == "streamed":
+        # RVEs too large for one CTA's shared memory: fiber data and CSR stream from L2/HBM (MODE 1/2)
+        nets, Fs = rvegen.config_uneven(152, side_lo=15, side_hi=16)
+        tol_m = tol_d = tol
     elif config == "orientation":
         nets, Fs = rvegen.config_uniform(1024)
         tol_m = tol_d = tol
@@ -136,6 +141,9 @@ def run(config: str, reps: int = 5, plain_subset: int = 32, tol: float = 3e-7, a
         res.update(batch_s=dt, rve_solves_per_s=n / dt, iters_mean=float(it.mean()), iters_max=int(it.max()),
                    converged_frac=float((st.cpu().numpy() == 0).mean()), bins=b.bins())
     m = min(plain_subset, n)
+    if m == 0:
+        b.close()
+        return res
     sub = rvegen.pack(nets[:m])
     pv, pit = _plain(sub, Fs[:m], tol_d, device, damping_scale)
     # the plain path solves from the affine start; for the tangent the batched
@@ -149,7 +157,7 @@ def run(config: str, reps: int = 5, plain_subset: int = 32, tol: float = 3e-7, a
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("config", choices=["single", "uneven", "tangent", "orientation"])
+    ap.add_argument("config", choices=["single", "uneven", "tangent", "orientation", "streamed"])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--plain-subset", type=int, default=32)
     ap.add_argument("--no-autotune", action="store_true")
