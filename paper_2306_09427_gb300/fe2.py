@@ -74,9 +74,9 @@ def first_pk_and_tangent(F, sigma, dsdF):
     Fi = np.linalg.inv(F)
     P = J[:, None, None] * np.einsum("nik,nJk->niJ", sigma, Fi)
     D = dsdF.reshape(-1, 3, 3, 3, 3)  # d sigma_ik / d F_mN
-    A = (J[:, None, None, None, None] * (np.einsum("nNm,nik,nJk->niJmN", Fi, sigma, Fi)
+    A = (J[:, None, None, None, None] * (np.einsum("nNm,nik,nJk->niJmN", Fi, sigma, Fi, optimize=True)
                                           + np.einsum("nikmN,nJk->niJmN", D, Fi)
-                                          - np.einsum("nik,nJm,nNk->niJmN", sigma, Fi, Fi)))
+                                          - np.einsum("nik,nJm,nNk->niJmN", sigma, Fi, Fi, optimize=True)))
     return P, A
 
 
@@ -134,7 +134,7 @@ class FE2:
         R = np.zeros((box.nn, 3))
         Re = box.vol * np.einsum("egiJ,gaJ->eai", P, box.G)
         np.add.at(R, box.conn, Re)
-        Ke = box.vol * np.einsum("gaJ,egiJkL,gbL->eaibk", box.G, A, box.G).reshape(box.ne, 24, 24)
+        Ke = box.vol * np.einsum("gaJ,egiJkL,gbL->eaibk", box.G, A, box.G, optimize=True).reshape(box.ne, 24, 24)
         K = sp.coo_matrix((Ke.ravel(), (self.rows, self.cols)), shape=(self.nd, self.nd)).tocsr()
         return R.ravel(), K, sigma, st
 
