@@ -12,17 +12,21 @@ precision:
   2. at each increment pin boundary nodes to x = F_k X (Eq. affine-bc) and
      predict free nodes as F_k X + h, h the previous fluctuation
      (Eq. micro_coords);
-  3. Newton on f_free(x) = 0 with K_ff + mu I factored by a sparse direct
-     solver (SuperLU, symmetric mode, diagonal pivots), mu raised until the
-     factor is positive definite so each step descends the stored energy,
-     and mu steered Levenberg-Marquardt style by the ratio of the actual to
-     the predicted energy decrease (the residual norm decides once energy
-     differences reach rounding);
+  3. Newton on f_free(x) = 0 with a sparse direct solver (SuperLU,
+     symmetric mode, diagonal pivots): the tangent K_ff is shifted by the
+     smallest mu in {0, 1e-12, 1e-11, ...} x mean diag K_ff that makes
+     K_ff + mu I positive definite (Levenberg-Marquardt-style regularisation
+     of floppy and compressed directions), so the step descends the stored
+     energy W; a backtracking line search halves the step until W drops by
+     the Armijo fraction 1e-4 of its predicted first-order decrease (once
+     that decrease reaches the rounding level of W, until ||f|| drops);
   4. stop at ||f_free||_2 <= max(tol * R_aff, 1e-16 sum EA) (R_aff from
      ``network.reference_force_scale``); after the last increment check
-     that K_ff is positive semi-definite (an energy minimum, not a saddle)
-     and, if not, push along the most negative curvature direction and
-     re-solve, at most three times;
+     that the state is an energy minimum, not a saddle: K_ff + s I with the
+     fixed shift s = 1e-9 x mean diag K_ff must factor with no negative pivot
+     (inertia by Sylvester's law); the lowest eigenvalue of K_ff is recorded
+     beside the verdict.  At a saddle, push along the lowest-curvature
+     direction and re-solve, at most three times;
   5. return sigma from the fiber virial and, as a self-check, from the
      boundary reactions (the two forms of the average after Eq. hill-mandel).
 
@@ -73,8 +77,10 @@ def _factor(K, mu):
                       options=dict(SymmetricMode=True))
     except RuntimeError:  # exactly singular: not positive definite
         return None, False, -1
+    # with symmetric (diagonal) pivots U = D L^T, so the signs of diag(U) give
+    # the inertia (Sylvester); after an off-diagonal pivot they do not (-1)
     symmetric_pivots = np.array_equal(lu.perm_r, lu.perm_c)
-    neg = int((lu.U.diagonal() <= 0).sum())
+    neg = int((lu.U.diagonal() <= 0).sum()) if symmetric_pivots else -1
     return lu, symmetric_pivots and neg == 0, neg
 
 
@@ -116,61 +122,80 @@ class _Problem:
 def _newton(pb, x, tol_abs, max_iter):
     """Energy-descending Newton on the free DOFs; returns (x, iters, ||r||, ok).
 
-    Levenberg-Marquardt trust region on the stored energy W: solve
-    (K + mu I) p = r with mu large enough for a positive definite factor,
-    accept when W decreases (gain ratio rho against the quadratic model),
-    divide mu by 10 after a good step (rho > 3/4), double it after a poor
-    one (rho < 1/4) or a rejected one.  Once the predicted decrease falls to the
-    rounding level of W, acceptance switches to a decrease of ||r||.
+    Each iteration factors K + mu I with the smallest mu of the sequence
+    0, 1e-12 d, 1e-11 d, ... (d = mean diag K) that gives a positive definite
+    factor, solves (K + mu I) p = r (r = -grad W), and backtracks along p:
+    the first step length a in 1, 1/2, 1/4, ... with
+    W(x + a p) <= W(x) - 1e-4 a (r . p) is taken; when a (r . p) is at the
+    rounding level of W, a step that lowers ||r|| is taken instead.
     """
-    mu, nu = 0.0, 2.0
     it = 0
     r = pb.residual(x)
     rn = float(np.linalg.norm(r))
     W0 = pb.energy(x)
-    K = None
     while rn > tol_abs and it < max_iter:
         it += 1
-        if K is None:
-            K = pb.tangent(x)
-            dscale = max(float(np.abs(K.diagonal()).mean()), 1e-300)
-            mu_min = 1e-12 * dscale
-        for _ in range(80):
+        K = pb.tangent(x)
+        dscale = max(float(np.abs(K.diagonal()).mean()), 1e-300)
+        mu = 0.0
+        for _ in range(40):
             lu, pd, _neg = _factor(K, mu)
             if pd:
                 break
-            mu = max(4.0 * mu, 1e-6 * dscale)
+            mu = 1e-12 * dscale if mu == 0.0 else 10.0 * mu
         else:
             return x, it, rn, False
         p = lu.solve(r)
-        pred = float(r @ p) - 0.5 * float(p @ (K @ p))
-        xt = pb.place(x, x[pb.free_ids].ravel() + p)
-        with np.errstate(over="ignore", invalid="ignore"):  # a wild trial step is rejected below
-            Wt = pb.energy(xt)
-            rt = pb.residual(xt)
-            rtn = float(np.linalg.norm(rt))
-        if pred > 1e-12 * max(abs(W0), 1e-300):
-            rho = (W0 - Wt) / pred
-            accept = rho > 1e-4 and np.isfinite(rtn)
+        slope = float(r @ p)  # predicted first-order decrease of W per unit step
+        a = 1.0
+        for _ in range(60):
+            xt = pb.place(x, x[pb.free_ids].ravel() + a * p)
+            with np.errstate(over="ignore", invalid="ignore"):  # a wild trial step is rejected below
+                Wt = pb.energy(xt)
+                rt = pb.residual(xt)
+                rtn = float(np.linalg.norm(rt))
+            if np.isfinite(rtn) and np.isfinite(Wt):
+                if a * slope > 1e-12 * max(abs(W0), 1e-300):
+                    if Wt <= W0 - 1e-4 * a * slope:
+                        break
+                elif rtn < rn:
+                    break
+            a *= 0.5
         else:
-            rho = 1.0
-            accept = rtn < rn
-        if accept:
-            x, r, rn, W0 = xt, rt, rtn, Wt
-            K = None
-            if rho > 0.75:
-                mu *= 0.1
-            elif rho < 0.25:
-                mu *= 2.0
-            if mu < mu_min:
-                mu = 0.0
-            nu = 2.0
-        else:
-            mu = max(mu * nu, 1e-6 * dscale)
-            nu *= 2.0
-            if mu > 1e14 * dscale:
-                return x, it, rn, False
+            return x, it, rn, False
+        x, r, rn, W0 = xt, rt, rtn, Wt
     return x, it, rn, rn <= tol_abs
+
+
+STAB_SHIFT = 1e-9  # fixed stability shift, relative to mean diag K_ff
+
+
+def lowest_eigenvalue(K):
+    """Lowest eigenvalue of the symmetric sparse K (dense up to 3000 DOF,
+    else a bounded Lanczos search; None if it does not converge)."""
+    n = K.shape[0]
+    if n == 0:
+        return None
+    if n <= 3000:
+        return float(np.linalg.eigvalsh(K.toarray())[0])
+    try:
+        return float(sla.eigsh(K, k=1, which="SA", tol=1e-8, maxiter=2000, return_eigenvectors=False)[0])
+    except sla.ArpackNoConvergence:
+        return None
+
+
+def stability(pb, x, with_lambda=True):
+    """(stable, lambda_min, negative pivots) of the free-DOF tangent at x
+    (lambda_min None unless with_lambda).
+
+    Stable means K_ff + s I, s = STAB_SHIFT * mean diag K_ff, has no negative
+    pivot in its symmetric factorisation, i.e. (Sylvester's law of inertia)
+    no eigenvalue of K_ff below -s: a local minimum of the stored energy up
+    to that fixed tolerance, which does not depend on the residual."""
+    K = pb.tangent(x)
+    dscale = max(float(np.abs(K.diagonal()).mean()), 1e-300)
+    _, pd, neg = _factor(K, STAB_SHIFT * dscale)
+    return bool(pd), (lowest_eigenvalue(K) if with_lambda else None), int(neg)
 
 
 def _lowest_mode(K):
@@ -194,12 +219,14 @@ def _lowest_mode(K):
 
 
 def solve(X, conn, L0, EA, B, is_boundary, F, V0=1.0, tol=1e-12, increments=1,
-          h0=None, max_newton=50000, check_stability=True, mid_tol=1e-6) -> Solution:
+          h0=None, max_newton=50000, check_stability=True, mid_tol=1e-6, record_lambda=False) -> Solution:
     """Equilibrium and Cauchy stress of one RVE under deformation gradient F.
 
     X (N,3), conn (E,2) RVE-local ids, L0/EA/B (E,), is_boundary (N,),
     F (3,3) with det F > 0.  ``h0`` (N,3) warm-starts the fluctuation
     h = x - F X; with a warm start the load is applied in one increment.
+    ``record_lambda`` adds the lowest eigenvalue of K_ff at the returned state
+    to ``info['lambda_min']`` (a dense or Lanczos eigensolve: a diagnostic).
     """
     X = np.asarray(X, np.float64).reshape(-1, 3)
     conn = np.asarray(conn).reshape(-1, 2).astype(np.int64)
@@ -238,18 +265,13 @@ def solve(X, conn, L0, EA, B, is_boundary, F, V0=1.0, tol=1e-12, increments=1,
         h = x - X @ Fk.T
     escapes = 0
     stable = None
+    lam_min = None
     if pb.free_ids.size and check_stability:
         for escapes in range(4):
-            K = pb.tangent(x)
-            dscale = max(float(np.abs(K.diagonal()).mean()), 1e-300)
-            # curvature below -shift counts as a saddle; a state converged only to
-            # residual r may show spurious negative eigenvalues of order r
-            rel_r = float(np.linalg.norm(pb.residual(x))) / max(R_ref, 1e-300)
-            _, pd, _ = _factor(K, max(1e-9, 10.0 * rel_r) * dscale)
-            stable = bool(pd)
+            stable, lam_min, _ = stability(pb, x, with_lambda=record_lambda)
             if stable or escapes == 3:
                 break
-            lam, vec = _lowest_mode(K)
+            _, vec = _lowest_mode(pb.tangent(x))
             step = 1e-3 * float(np.mean(l0)) * vec / max(np.abs(vec).max(), 1e-300)
             x = pb.place(x, x[pb.free_ids].ravel() + step)
             x, it, rn, ok = _newton(pb, x, convergence_threshold(tol, R_ref, ea), max_newton)
@@ -261,7 +283,8 @@ def solve(X, conn, L0, EA, B, is_boundary, F, V0=1.0, tol=1e-12, increments=1,
     return Solution(sigma=sigma, sigma_boundary=sigma_b, x=x, residual=rn, R_ref=R_ref,
                     converged=bool(rn <= convergence_threshold(tol, R_ref, ea)), newton_iters=total_it, stable=stable,
                     saddle_escapes=escapes, kept=kept, free=free,
-                    info=dict(n_free=int(pb.free_ids.size), n_fibers=int(kept.sum())))
+                    info=dict(n_free=int(pb.free_ids.size), n_fibers=int(kept.sum()), lambda_min=lam_min,
+                              energy=float(pb.energy(x))))
 
 
 def solve_network(net, F, **kw) -> Solution:
