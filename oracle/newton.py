@@ -24,9 +24,11 @@ precision:
      ``network.reference_force_scale``); after the last increment check
      that the state is an energy minimum, not a saddle: K_ff + s I with the
      fixed shift s = 1e-9 x mean diag K_ff must factor with no negative pivot
-     (inertia by Sylvester's law); the lowest eigenvalue of K_ff is recorded
-     beside the verdict.  At a saddle, push along the lowest-curvature
-     direction and re-solve, at most three times;
+     (inertia by Sylvester's law); the lowest eigenvalue of K_ff can be
+     recorded beside the verdict.  At a saddle, push along the
+     lowest-curvature direction and re-solve, at most three times.  The
+     verdict is taken for solves converged to a relative residual of 1e-8 or
+     below (by default; it needs the state converged well below the shift);
   5. return sigma from the fiber virial and, as a self-check, from the
      boundary reactions (the two forms of the average after Eq. hill-mandel).
 
@@ -124,7 +126,8 @@ def _newton(pb, x, tol_abs, max_iter):
 
     Each iteration factors K + mu I with the smallest mu of the sequence
     0, 1e-12 d, 1e-11 d, ... (d = mean diag K) that gives a positive definite
-    factor, solves (K + mu I) p = r (r = -grad W), and backtracks along p:
+    factor (the search starts a decade below the previous iteration's shift),
+    solves (K + mu I) p = r (r = -grad W), and backtracks along p:
     the first step length a in 1, 1/2, 1/4, ... with
     W(x + a p) <= W(x) - 1e-4 a (r . p) is taken; when a (r . p) is at the
     rounding level of W, a step that lowers ||r|| is taken instead.
@@ -133,11 +136,12 @@ def _newton(pb, x, tol_abs, max_iter):
     r = pb.residual(x)
     rn = float(np.linalg.norm(r))
     W0 = pb.energy(x)
+    mu_rel = 0.0  # last shift that worked, relative to mean diag K (the search starts a decade below it)
     while rn > tol_abs and it < max_iter:
         it += 1
         K = pb.tangent(x)
         dscale = max(float(np.abs(K.diagonal()).mean()), 1e-300)
-        mu = 0.0
+        mu = 0.1 * mu_rel * dscale if mu_rel >= 1e-11 else 0.0
         for _ in range(40):
             lu, pd, _neg = _factor(K, mu)
             if pd:
@@ -145,6 +149,7 @@ def _newton(pb, x, tol_abs, max_iter):
             mu = 1e-12 * dscale if mu == 0.0 else 10.0 * mu
         else:
             return x, it, rn, False
+        mu_rel = mu / dscale
         p = lu.solve(r)
         slope = float(r @ p)  # predicted first-order decrease of W per unit step
         a = 1.0
@@ -168,6 +173,7 @@ def _newton(pb, x, tol_abs, max_iter):
 
 
 STAB_SHIFT = 1e-9  # fixed stability shift, relative to mean diag K_ff
+STAB_TOL = 1e-8    # solves at or below this relative residual assess stability by default
 
 
 def lowest_eigenvalue(K):
@@ -219,12 +225,15 @@ def _lowest_mode(K):
 
 
 def solve(X, conn, L0, EA, B, is_boundary, F, V0=1.0, tol=1e-12, increments=1,
-          h0=None, max_newton=50000, check_stability=True, mid_tol=1e-6, record_lambda=False) -> Solution:
+          h0=None, max_newton=50000, check_stability=None, mid_tol=1e-6, record_lambda=False) -> Solution:
     """Equilibrium and Cauchy stress of one RVE under deformation gradient F.
 
     X (N,3), conn (E,2) RVE-local ids, L0/EA/B (E,), is_boundary (N,),
     F (3,3) with det F > 0.  ``h0`` (N,3) warm-starts the fluctuation
     h = x - F X; with a warm start the load is applied in one increment.
+    ``check_stability`` None assesses stability (and escapes saddles) when
+    tol <= STAB_TOL only: a fixed-shift inertia verdict needs a state converged
+    well below the shift, and at looser tolerances ``stable`` stays None.
     ``record_lambda`` adds the lowest eigenvalue of K_ff at the returned state
     to ``info['lambda_min']`` (a dense or Lanczos eigensolve: a diagnostic).
     """
@@ -266,6 +275,8 @@ def solve(X, conn, L0, EA, B, is_boundary, F, V0=1.0, tol=1e-12, increments=1,
     escapes = 0
     stable = None
     lam_min = None
+    if check_stability is None:
+        check_stability = tol <= STAB_TOL
     if pb.free_ids.size and check_stability:
         for escapes in range(4):
             stable, lam_min, _ = stability(pb, x, with_lambda=record_lambda)
