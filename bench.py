@@ -34,16 +34,28 @@ TOL = 3e-7          # relative residual of the mixed path (library default; sigm
 SIGMA_TOL = 0.0     # stress-convergence criterion off (library default)
 DAMPING_SCALE = 0.7  # c = 0.7 * 2 sqrt(lambda_RQ) on both paths timed (parity-tested at this setting)
 PLAIN_SUBSET = 32   # RVEs timed on the plain FP64 per-RVE path
-# algorithmic FP32 work per fiber-update (FMA = 2 flops): fiber force 39
-# (chord update 3, Green strain 13, length 6, law 4, stiffness bound 7,
-# force vector 3, misc 3) + CSR gather 8 (4 adds at each end)
-FLOPS_PER_FIBER_UPDATE = 47.0
-FLOPS_PER_NODE_UPDATE = 17.0   # lumped mass, damped velocity, cap, position
+F_STEP = 1e-3       # step k solves F + k F_STEP G (G fixed, |G_ij| <= 1): a small increment per step
+# Algorithmic work of one DR iteration (the method's own count, FMA = 2
+# flops): about 30 FP32 flops + 1 exp + 1 rsqrt per fiber-update (chord,
+# strain, length, law, force vector) and about 20 per free-node update
+# (gathered force, damped velocity, position).
+FLOPS_PER_FIBER_UPDATE = 30.0
+FLOPS_PER_NODE_UPDATE = 20.0
+# this kernel's own count, reported beside it: fiber force 39 (adds the
+# stiffness bound 7, chord update 3, misc 3) + CSR gather 8; node 17
+IMPL_FLOPS_PER_FIBER_UPDATE = 47.0
+IMPL_FLOPS_PER_NODE_UPDATE = 17.0
+# Algorithmic on-chip bytes of one DR iteration: per active fiber its two
+# endpoint indices and three parameters (20 B), per free node h and v read
+# and written plus 1/m (52 B); boundary nodes are not stored (zero slot).
+BYTES_PER_FIBER_UPDATE = 20.0
+BYTES_PER_NODE_UPDATE = 52.0
 FP32_LANES_PER_SM = 128
+SMEM_BYTES_PER_CLK_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused-kernel launch on
-# this workload (ncu capture summarised in profiles/dr_fused_uniform1024_full.md);
-# None whenever the kernel changes after that capture
-TRAFFIC_BYTES_PER_LAUNCH = 105.62e6 + 5.48e6
+# this workload (ncu capture summarised in profiles/); None whenever the
+# kernel changes after that capture
+TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def _config():
@@ -51,8 +63,9 @@ def _config():
                         "random F=R.U (principal strains U[-0.05,0.15])",
             "n_rve": N_RVE, "grid_side": SIDE, "tol_rel_residual": TOL, "sigma_tol": SIGMA_TOL,
             "damping_scale": DAMPING_SCALE, "precision": "mixed (FP32 forces/updates, "
-            "FP64 residual and stress sums)", "start": "cold (h=0) every step", "l2": "flushed between timed steps "
-            "(256 MiB write)"}
+            "FP64 residual and stress sums)", "start": "cold (h=0) every step",
+            "F_per_step": f"step k solves F + k*{F_STEP:g}*G (G fixed, entries in [-1,1]): no two steps repeat F",
+            "l2": "flushed between timed steps (256 MiB write)"}
 
 
 def _dist():
@@ -209,18 +222,33 @@ def run_ours(args, rank, world, local):
     pk = rvegen.pack(nets)
     b = rve.RveBatch(pk, device=local, precision=rve.RVE_PREC_MIXED, tol=TOL, sigma_tol=SIGMA_TOL, warm_start=0,
                      damping_scale=DAMPING_SCALE)
-    Fd = torch.tensor(Fs.reshape(-1, 9), dtype=torch.float64, device=dev)
+    # per-step deformation gradients, all resident before timing
+    G = rvegen.Stream(0x5EEDF00D + rank).uniform(9 * N_RVE, -1.0, 1.0).reshape(N_RVE, 9)
+    n_steps = args.warmup + args.steps
+    F_all = np.stack([Fs.reshape(-1, 9) + k * F_STEP * G for k in range(n_steps + 1)])
+    Fd_all = torch.tensor(F_all, dtype=torch.float64, device=dev)
     sigma = torch.empty((N_RVE, 9), dtype=torch.float64, device=dev)
-    iters = torch.empty(N_RVE, dtype=torch.int32, device=dev)
+    iters_all = torch.empty((n_steps + 1, N_RVE), dtype=torch.int32, device=dev)  # each step's own counts
+    iters = iters_all[n_steps]
     status = torch.empty(N_RVE, dtype=torch.int32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
-        b.solve(Fd, sigma=sigma, iters=iters, status=status, stream=stream)
+    def step(k):
+        b.solve(Fd_all[k], sigma=sigma, iters=iters_all[k], status=status, stream=stream)
 
-    for _ in range(args.warmup):
-        step()
+    # the first solve of a fresh batch: no learned per-RVE cost for the
+    # longest-first order yet (set-up of the size bins excluded: done by a
+    # solve of another batch object of the same networks)
+    b_cold = rve.RveBatch(pk, device=local, precision=rve.RVE_PREC_MIXED, tol=TOL, sigma_tol=SIGMA_TOL,
+                          warm_start=0, damping_scale=DAMPING_SCALE)
+    b_cold.set_kernel_timing(True)
+    b_cold.solve(Fd_all[0], sigma=sigma, iters=iters, status=status, stream=stream)
+    torch.cuda.synchronize()
+    first_solve_ms = float(b_cold.last_kernel_ms().sum())
+    b_cold.close()
+    for k in range(args.warmup):
+        step(k)
     torch.cuda.synchronize()
     n_bins = b.info()["n_bins"]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -237,7 +265,7 @@ def run_ours(args, rank, world, local):
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
-        step()
+        step(args.warmup + k)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop(t_win0, time.time())
@@ -245,9 +273,9 @@ def run_ours(args, rank, world, local):
     kernel_ms = b.last_kernel_ms()  # n_bins launches per step
     b.set_kernel_timing(False)
     t_total = sum(step_ms) / 1e3
-    it = iters.cpu().numpy()
+    it_steps = iters_all[args.warmup:args.warmup + args.steps].cpu().numpy()  # (steps, N_RVE)
+    it = it_steps[-1]
     st = status.cpu().numpy()
-    it_total = int(it.sum())
     if world > 1:
         t = torch.tensor([t_total], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -255,25 +283,29 @@ def run_ours(args, rank, world, local):
     value = world * N_RVE * args.steps / t_total
     # fiber-updates and roofline of the fused kernel (one launch per bin per step)
     nf, na, _ = b.sizes()
-    fiber_updates = float((na.astype(np.float64) * it).sum())
-    node_updates = float((nf.astype(np.float64) * it).sum())
+    fiber_updates = float((na.astype(np.float64) * it_steps).sum()) / args.steps  # per step
+    node_updates = float((nf.astype(np.float64) * it_steps).sum()) / args.steps
     t_step = t_total / args.steps
     # the dominant kernel: the fused solve; with one bin it is one launch per step,
     # with several (concurrent) bins their summed durations bound the kernel time
     t_kernel = float(kernel_ms.sum()) / 1e3 / args.steps
     flops = FLOPS_PER_FIBER_UPDATE * fiber_updates + FLOPS_PER_NODE_UPDATE * node_updates
+    impl_flops = IMPL_FLOPS_PER_FIBER_UPDATE * fiber_updates + IMPL_FLOPS_PER_NODE_UPDATE * node_updates
+    onchip = BYTES_PER_FIBER_UPDATE * fiber_updates + BYTES_PER_NODE_UPDATE * node_updates
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clocks.get("sm_mhz") or 2070.0
     peak = sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
     achieved = flops / t_kernel / 1e12
+    smem_peak = sm_count * SMEM_BYTES_PER_CLK_PER_SM * mhz * 1e6 / 1e9
+    smem_achieved = onchip / t_kernel / 1e9
 
     # end to end through the public host-buffer call (copies inside)
     e2e_steps = max(1, min(args.steps, 5))
-    b.solve_host(Fs)  # staging buffers allocated outside the timed region
+    b.solve_host(F_all[0])  # staging buffers allocated outside the timed region
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        b.solve_host(Fs)
+    for k in range(e2e_steps):
+        b.solve_host(F_all[k + 1])
     e2e = N_RVE * e2e_steps / (time.perf_counter() - t0)
 
     # plain FP64 per-RVE path on a subset (one RVE at a time, several launches per iteration)
@@ -283,10 +315,10 @@ def run_ours(args, rank, world, local):
         bp = rve.RveBatch(sub, device=local, precision=rve.RVE_PREC_PLAIN_F64, tol=TOL, sigma_tol=SIGMA_TOL,
                           damping_scale=DAMPING_SCALE)
         sp = torch.empty((PLAIN_SUBSET, 9), dtype=torch.float64, device=dev)
-        bp.solve(Fd[:PLAIN_SUBSET].contiguous(), sigma=sp)
+        bp.solve(Fd_all[0, :PLAIN_SUBSET].contiguous(), sigma=sp)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        bp.solve(Fd[:PLAIN_SUBSET].contiguous(), sigma=sp)
+        bp.solve(Fd_all[1, :PLAIN_SUBSET].contiguous(), sigma=sp)
         torch.cuda.synchronize()
         plain = PLAIN_SUBSET / (time.perf_counter() - t0)
         bp.close()
@@ -305,10 +337,20 @@ def run_ours(args, rank, world, local):
                      "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_LAUNCH, "traffic_unit": "bytes per launch",
                      "kernel_ms_per_launch": float(kernel_ms.mean()), "launches_timed": int(kernel_ms.size),
                      "kernel": "dr_fused_kernel<float,...> (one CTA per RVE, resident in shared memory)",
+                     "work": f"{FLOPS_PER_FIBER_UPDATE:g} flops per fiber-update + {FLOPS_PER_NODE_UPDATE:g} per "
+                             "free-node update (algorithmic)",
+                     "impl_flops_frac": impl_flops / t_kernel / 1e12 / peak,
                      "peak_note": f"FP32 FMA peak derived: {sm_count} SMs x 128 lanes x 2 flops x {mhz:.0f} MHz "
                                   "(median SM clock under load)"},
+        "roofline_smem": {"bound": "smem", "achieved": smem_achieved, "peak": smem_peak, "unit": "GB/s",
+                          "frac": smem_achieved / smem_peak,
+                          "work": f"{BYTES_PER_FIBER_UPDATE:g} B per fiber-update + {BYTES_PER_NODE_UPDATE:g} B per "
+                                  "free-node update (algorithmic on-chip bytes)",
+                          "peak_note": f"{sm_count} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x {mhz:.0f} MHz"},
+        "first_solve_ms": first_solve_ms,
         "fiber_updates_per_s": fiber_updates / t_step,
-        "iterations": {"mean": float(it.mean()), "max": int(it.max()), "converged_frac": float((st == 0).mean())},
+        "iterations": {"mean": float(it_steps.mean()), "max": int(it_steps.max()),
+                       "converged_frac_last_step": float((st == 0).mean())},
         "plain_fp64_per_rve": {"value": plain, "unit": UNIT, "subset": f"first {PLAIN_SUBSET} RVEs, same tol"}
         if plain else None,
         "speedup_vs_plain": (value / world) / plain if plain else None,

@@ -55,6 +55,9 @@ extern "C" {
 #define RVE_STATUS_NONFINITE 2 /* residual became NaN/Inf; sigma is not meaningful */
 #define RVE_STATUS_EMPTY 3     /* no free node left after pruning; sigma is exact
                                   (boundary-to-boundary fibers only), 0 iterations  */
+#define RVE_STATUS_RUNNING 4   /* serving only: the wave ended before the solve did;
+                                  the solve is parked on the device and resumes in
+                                  the next wave (never returned by rve_server_poll) */
 
 /* precision / execution path */
 #define RVE_PREC_PLAIN_F64 0   /* one RVE at a time, several FP64 kernels per DR
@@ -115,6 +118,23 @@ typedef struct rve_batch rve_batch; /* opaque, library owned */
  *               uneven workloads, but one 16^3 network solved in FP64 to
  *               1e-10 with it stopped on a weakly unstable equilibrium.
  *               Must be in (0, 1]; 0 means the default.
+ *  energy_check 1: the all-RVE solves (rve_solve) run the kernel variant
+ *               with Algorithm 2's optional energy balance (Sec. 3.2, after
+ *               Belytschko).  At every check it evaluates the stored energy
+ *               of the active fibers exactly (8-point Gauss-Legendre of the
+ *               axial force per fiber), so its change dW from the start; the
+ *               kinetic energy K of the last half step; and from sums over
+ *               the steps the kinetic energy lost to damping D and to the
+ *               step cap C, and the work M of the fictitious mass changes.
+ *               K + D + C - M equals the trapezoidal rule of the force work
+ *               along the iterates, so the balance error
+ *               |dW + K + D + C - M + v.f/2| / max(|dW|, K, D + C) (v.f/2
+ *               the pending half step) is the quadrature error of the
+ *               central-difference steps, the time-integration error the
+ *               check exists to expose; the largest over the checks is kept.
+ *               Read the records with rve_energy.  Batched precisions with
+ *               viscous damping only (RVE_EINVAL otherwise); diagnostic, the
+ *               iterates are those of the default kernel.  Default 0.
  */
 typedef struct rve_options {
   double tol;
@@ -127,7 +147,7 @@ typedef struct rve_options {
   int32_t graphs;
   double sigma_tol;
   int32_t damping_mode;
-  int32_t reserved0;
+  int32_t energy_check;
   double damping_scale;
 } rve_options;
 
@@ -221,15 +241,32 @@ int rve_solve_host(rve_batch* b, const double* F, double tol, int32_t max_iter, 
  * Always starts from h = 0 and leaves the batch's warm-start state alone.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress) for that device; make that first call before any
- * stream capture.  All calls, on any batch, share the one array and the
- * call returns only after the solve's last convergence check: calls that
- * overlap on the GPU (from several host threads) race and must be
- * serialised by the caller.
+ * stream capture.  All calls, on any batch, share the one array.  The call
+ * returns after the solve's last convergence check, but its stress and
+ * finishing kernels are still queued on `stream` and read the array: a
+ * second call on another stream, from this thread or any other, races with
+ * them unless the caller orders the two (an event recorded on the first
+ * call's stream and waited on by the second's, or a synchronisation of the
+ * first call's stream).  Calls on one stream are ordered by the stream.
  */
 #define RVE_NOALLOC_MAX_ACTIVE_FIBERS 16384
 #define RVE_NOALLOC_MAX_FREE_NODES 8192
 int rve_solve_plain_noalloc(rve_batch* b, int64_t r, const double* F, double tol, int32_t max_iter,
                             double* sigma, int32_t* iters, int32_t* status, void* stream);
+
+/*
+ * Energy records of the last rve_solve run with the option energy_check = 1,
+ * on the given batched precision.  energy: DEVICE, 6 doubles per RVE:
+ *   [0] dW   change of stored energy from the start state (<= 0 when relaxing)
+ *   [1] K    kinetic energy of the last half step at the last check
+ *   [2] D    kinetic energy lost to viscous damping
+ *   [3] C    further kinetic energy lost (the step cap)
+ *   [4] M    work of the fictitious mass changes
+ *   [5] the largest relative balance error over the checks (option
+ *        energy_check).
+ * Asynchronous on stream.  RVE_EINVAL before any such solve.
+ */
+int rve_energy(rve_batch* b, int32_t precision, double* energy, void* stream);
 
 /*
  * Stress and stress tangent: sigma(F) and the central-difference
@@ -359,40 +396,68 @@ int rve_get_positions(rve_batch* b, int64_t r, const double* F, int32_t precisio
                       double* x_out);
 
 /*
- * Continuous-batching request loop (serving).  The paper's RVE batch
- * manager (Sec. 4.3) hands one batched solve per macroscale iteration to the
- * GPU; the server instead takes single requests (rve id, F) as they arrive
- * and keeps the GPU busy with overlapping waves:
+ * Continuous-batching request loop (serving) over a resident pool of RVEs.
+ * The paper's RVE batch manager (Sec. 4.3) hands one batched solve per
+ * macroscale iteration to the GPU; the server instead takes single requests
+ * (rve id, F) as they arrive and batches them at the granularity of DR
+ * iterations (Algorithm 2's loop):
  *   - requests queue on the host in arrival order;
- *   - each of n_slots CUDA streams, when free, launches a wave of up to
- *     max_wave queued requests (an RVE already on the GPU waits, so its
- *     warm-start state is advanced by one solve at a time);
- *   - rve_server_step retires finished waves (event query, non-blocking)
- *     and fills free slots; rve_server_drain blocks until the queue is
- *     empty and no wave is in flight;
+ *   - the server has n_slots wave groups (CUDA streams), each with max_wave
+ *     request slots; a group runs one wave at a time, and a wave advances
+ *     every occupied slot by wave_iters DR iterations (rve_server_set_wave_iters;
+ *     0, the default, runs every request to its end within one wave); a solve
+ *     that is not done parks on the device (positions, velocities, damping
+ *     and iteration count) and resumes in the group's next wave;
+ *   - between waves finished requests retire and queued ones take the free
+ *     slots; an RVE is in at most one slot at a time, so its warm-start
+ *     state advances by one request at a time;
+ *   - each request's iterates depend only on its own F, its start state and
+ *     wave_iters, so its result is bit-identical alone and in any mix;
+ *   - rve_server_step retires finished waves (event query, non-blocking),
+ *     admits queued requests and launches the next waves; rve_server_drain
+ *     blocks until the queue is empty and no request is on the GPU;
  *   - rve_server_poll returns finished results in completion order with
- *     their latency (seconds from submit to the step that saw the wave done).
- * The batch's options apply (precision, tolerance, warm_start: with
- * warm_start = 1 every RVE keeps its converged state on the device between
- * requests).  The plain FP64 path allows n_slots = 1 only.
- * Admission: RVE_EADMIT when the batch's device memory plus the server's
- * buffers exceed hbm_cap_bytes (<= 0: no cap).  The batch must outlive the
- * server; one host thread drives a server.  Waves of one server run
- * concurrently (each slot has its own work buffers; an RVE is in at most one
- * wave); call rve_server_drain before using the batch through the other
- * rve_* calls, whose GPU work is ordered after the batch's previous call only.
+ *     their latency (seconds from submit to the step that saw them done).
+ * The batch's options apply to every solve (precision, tolerance,
+ * warm_start: with warm_start = 1 every RVE keeps its converged state on the
+ * device between requests).  The plain FP64 path allows n_slots = 1 and
+ * wave_iters = 0 only.
+ * Pool and admission by device memory (hbm_cap_bytes <= 0: no cap):
+ *   - rve_server_create: RVE_EADMIT when the batch, its solver state and the
+ *     server's buffers exceed the cap;
+ *   - rve_server_add_rves: admits more RVE topologies (arguments as
+ *     rve_batch_create, HOST arrays, the batch's options) as a new group of
+ *     the pool; their global ids are *first_id .. *first_id + n_rve - 1 (ids
+ *     are assigned in admission order and never reused).  RVE_EADMIT, with
+ *     nothing admitted, when their device footprint would take the pool over
+ *     the cap;
+ *   - rve_server_remove_rves: frees the group admitted with first_id (no
+ *     request for it may be queued or in flight); the batch given at
+ *     creation stays.
+ * The batch given at creation must outlive the server; one host thread
+ * drives a server; call rve_server_drain before using that batch through the
+ * other rve_* calls (which also clears parked solves' state).
  */
 typedef struct rve_server rve_server;
 typedef struct rve_server_stats {
-  int64_t queued;       /* waiting on the host                       */
-  int64_t in_flight;    /* in waves on the GPU                       */
-  int64_t ready;        /* finished, not yet polled                  */
-  int64_t completed;    /* finished since creation                   */
-  int64_t waves;        /* waves launched since creation             */
-  int64_t device_bytes; /* device memory of the server's own buffers */
+  int64_t queued;            /* waiting on the host                         */
+  int64_t in_flight;         /* in slots on the GPU (running or parked)     */
+  int64_t ready;             /* finished, not yet polled                    */
+  int64_t completed;         /* finished since creation                     */
+  int64_t waves;             /* waves launched since creation               */
+  int64_t device_bytes;      /* device memory of the server's own buffers   */
+  int64_t pool_rves;         /* RVEs in the pool                            */
+  int64_t pool_device_bytes; /* device memory of the pool's batches + state */
+  int64_t wave_iters;        /* DR iterations per wave (0: to the end)      */
 } rve_server_stats;
 int rve_server_create(rve_server** out, rve_batch* b, int32_t n_slots, int32_t max_wave, double hbm_cap_bytes);
-/* Queue one request; F is a HOST array of 9 doubles (copied). */
+/* Iterations per wave (>= 0); only while no request is on the GPU. */
+int rve_server_set_wave_iters(rve_server* s, int32_t wave_iters);
+int rve_server_add_rves(rve_server* s, int64_t n_rve, const int64_t* node_off, const double* X,
+                        const int64_t* fiber_off, const int32_t* conn, const double* L0, const double* EA,
+                        const double* B, const uint8_t* is_boundary, const double* V0, int64_t* first_id);
+int rve_server_remove_rves(rve_server* s, int64_t first_id);
+/* Queue one request for global RVE id rve_id; F is a HOST array of 9 doubles (copied). */
 int rve_server_submit(rve_server* s, int64_t rve_id, const double* F, int64_t tag);
 int rve_server_step(rve_server* s);
 int rve_server_drain(rve_server* s);

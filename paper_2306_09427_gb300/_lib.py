@@ -14,6 +14,7 @@ lib = C.CDLL(lib_path)
 
 RVE_OK, RVE_EINVAL, RVE_ENOMEM, RVE_ECUDA, RVE_EADMIT = 0, -1, -2, -3, -4
 RVE_STATUS_CONVERGED, RVE_STATUS_MAX_ITER, RVE_STATUS_NONFINITE, RVE_STATUS_EMPTY = 0, 1, 2, 3
+RVE_STATUS_RUNNING = 4
 RVE_PREC_PLAIN_F64, RVE_PREC_MIXED, RVE_PREC_BATCHED_F64 = 0, 1, 2
 RVE_DAMP_VISCOUS, RVE_DAMP_KINETIC = 0, 1
 
@@ -22,7 +23,7 @@ class rve_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("check_every", C.c_int32),
                 ("precision", C.c_int32), ("warm_start", C.c_int32), ("damping", C.c_double),
                 ("threads", C.c_int32), ("graphs", C.c_int32), ("sigma_tol", C.c_double),
-                ("damping_mode", C.c_int32), ("reserved0", C.c_int32), ("damping_scale", C.c_double)]
+                ("damping_mode", C.c_int32), ("energy_check", C.c_int32), ("damping_scale", C.c_double)]
 
 
 class rve_batch_info(C.Structure):
@@ -55,6 +56,7 @@ RVE_NOALLOC_MAX_ACTIVE_FIBERS, RVE_NOALLOC_MAX_FREE_NODES = 16384, 8192
 rve_tangent = _sig("rve_tangent", C.c_int, [_P, _P, _D, _D, _I32, _P, _P, _P, _P])
 rve_tangent_mandel = _sig("rve_tangent_mandel", C.c_int, [_P, _P, _D, _D, _I32, _P, _P, _P, _P])
 rve_orientation = _sig("rve_orientation", C.c_int, [_P, _P, _I32, _P, _P])
+rve_energy = _sig("rve_energy", C.c_int, [_P, _I32, _P, _P])
 rve_reset_state = _sig("rve_reset_state", C.c_int, [_P, _P, _I64])
 rve_batch_get_info = _sig("rve_batch_get_info", C.c_int, [_P, C.POINTER(rve_batch_info)])
 rve_batch_get_sizes = _sig("rve_batch_get_sizes", C.c_int, [_P, _P, _P, _P])
@@ -74,11 +76,16 @@ rve_batch_destroy = _sig("rve_batch_destroy", None, [_P])
 
 
 class rve_server_stats(C.Structure):
-    _fields_ = [(n, C.c_int64) for n in ("queued", "in_flight", "ready", "completed", "waves", "device_bytes")]
+    _fields_ = [(n, C.c_int64) for n in ("queued", "in_flight", "ready", "completed", "waves", "device_bytes",
+                                         "pool_rves", "pool_device_bytes", "wave_iters")]
 
 
 rve_server_create = _sig("rve_server_create", C.c_int, [C.POINTER(_P), _P, _I32, _I32, _D])
 rve_server_submit = _sig("rve_server_submit", C.c_int, [_P, _I64, _P, _I64])
+rve_server_set_wave_iters = _sig("rve_server_set_wave_iters", C.c_int, [_P, _I32])
+rve_server_add_rves = _sig("rve_server_add_rves", C.c_int, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                                            C.POINTER(_I64)])
+rve_server_remove_rves = _sig("rve_server_remove_rves", C.c_int, [_P, _I64])
 rve_server_step = _sig("rve_server_step", C.c_int, [_P])
 rve_server_drain = _sig("rve_server_drain", C.c_int, [_P])
 rve_server_poll = _sig("rve_server_poll", C.c_int64, [_P, _I64, _P, _P, _P, _P, _P])
@@ -291,6 +298,15 @@ class RveBatch:
             raise RveError(m, "rve_last_kernel_ms")
         return out[:n]
 
+    def energy(self, precision: int | None = None, stream=None):
+        """Energy records (n_rve, 6) of the last solve with energy_check = 1:
+        dW, K, D, C, M and the largest relative balance error."""
+        import torch
+        prec = self.opt.precision if precision is None else precision
+        out = torch.empty((self.n_rve, 6), dtype=torch.float64, device=f"cuda:{self.device}")
+        _check(rve_energy(self.h, prec, _ptr(out), _stream_handle(stream)), "rve_energy")
+        return out.cpu().numpy()
+
     def reset_state(self, ids=None) -> None:
         if ids is None:
             _check(rve_reset_state(self.h, None, 0), "rve_reset_state")
@@ -307,14 +323,39 @@ class RveBatch:
 
 
 class RveServer:
-    """Owner of an ``rve_server`` handle (continuous batching over a batch)."""
+    """Owner of an ``rve_server`` handle (continuous batching over a resident
+    pool: the batch given here plus groups admitted by ``add_rves``)."""
 
-    def __init__(self, batch: RveBatch, n_slots: int = 4, max_wave: int = 1024, hbm_cap_bytes: float = 150e9):
+    def __init__(self, batch: RveBatch, n_slots: int = 4, max_wave: int = 1024, hbm_cap_bytes: float = 150e9,
+                 wave_iters: int = 0):
         self.batch = batch
         h = _P()
         _check(rve_server_create(C.byref(h), batch.h, n_slots, max_wave, hbm_cap_bytes), "rve_server_create")
         self.h = h
         self._F = np.zeros(9)
+        if wave_iters:
+            self.set_wave_iters(wave_iters)
+
+    def set_wave_iters(self, wave_iters: int) -> None:
+        _check(rve_server_set_wave_iters(self.h, wave_iters), "rve_server_set_wave_iters")
+
+    def add_rves(self, packed) -> int:
+        """Admit the networks of ``packed`` (rvegen.Packed layout) into the
+        pool; returns the global id of the first (RveError RVE_EADMIT when
+        they do not fit under the cap)."""
+        p = packed
+        keep = [np.ascontiguousarray(p.node_off, np.int64), np.ascontiguousarray(p.X, np.float64),
+                np.ascontiguousarray(p.fiber_off, np.int64), np.ascontiguousarray(p.conn, np.int32),
+                np.ascontiguousarray(p.L0, np.float64), np.ascontiguousarray(p.EA, np.float64),
+                np.ascontiguousarray(p.B, np.float64), np.ascontiguousarray(p.is_boundary, np.uint8),
+                None if p.V0 is None else np.ascontiguousarray(p.V0, np.float64)]
+        first = _I64(-1)
+        _check(rve_server_add_rves(self.h, keep[0].shape[0] - 1, *[_ptr(a) for a in keep], C.byref(first)),
+               "rve_server_add_rves")
+        return int(first.value)
+
+    def remove_rves(self, first_id: int) -> None:
+        _check(rve_server_remove_rves(self.h, first_id), "rve_server_remove_rves")
 
     def submit(self, rve_id: int, F, tag: int) -> None:
         self._F[:] = np.asarray(F, np.float64).reshape(9)

@@ -54,6 +54,7 @@ struct PathState {
   void* d_gP0 = nullptr;        // streamed-bin scratch (4 T per active fiber)
   void* d_gP1 = nullptr;
   void* d_gSCR = nullptr;
+  double* d_energy = nullptr;   // energy_check: 6 doubles per RVE of the last all-RVE solve
   void* d_tan_state = nullptr;  // 18 x 4 doubles per free node
   void* d_tan_g[3] = {};        // streamed-bin scratch of the tangent directions
   std::vector<int> bin_of;      // per RVE: index into bins
@@ -79,6 +80,20 @@ struct SubsetBuffers {
 int solve_subset(rve_batch* b, const int64_t* ids, int64_t m, const double* F, double tol, int32_t max_iter,
                  double* sigma, int32_t* iters, int32_t* status, cudaStream_t s, bool fork,
                  const SubsetBuffers* ext);
+// Iteration-level waves: solves stop after wave_iters iterations and park
+// (resume: one record per RVE of the batch; vel: 4 T per free node).
+struct WaveParams {
+  int32_t wave_iters = 0;
+  ResumeRec* resume = nullptr;
+  void* vel = nullptr;
+};
+// Subset solve writing item k's outputs (and reading its F) at index outs[k]
+// (k when outs is null), optionally as one wave.
+int solve_items(rve_batch* b, const int64_t* ids, const int32_t* outs, int64_t m, const double* F, double tol,
+                int32_t max_iter, double* sigma, int32_t* iters, int32_t* status, cudaStream_t s, bool fork,
+                const SubsetBuffers* ext, const WaveParams* wave);
+// Bring up the batched path of the batch's precision (bins, state buffers).
+int ensure_batched_path(rve_batch* b);
 constexpr int N_DIRS = 18;  // 9 directions x (+h, -h)
 
 }  // namespace rvegpu

@@ -27,9 +27,12 @@ int launch_bin_viscous(const DrArgs<float>& a, const Bin& bin, cudaStream_t s);
 int launch_bin_viscous(const DrArgs<double>& a, const Bin& bin, cudaStream_t s);
 int launch_bin_kinetic(const DrArgs<float>& a, const Bin& bin, cudaStream_t s);
 int launch_bin_kinetic(const DrArgs<double>& a, const Bin& bin, cudaStream_t s);
+int launch_bin_energy(const DrArgs<float>& a, const Bin& bin, cudaStream_t s);
+int launch_bin_energy(const DrArgs<double>& a, const Bin& bin, cudaStream_t s);
 template <typename T>
 int launch_bin(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
-  return a.kinetic ? launch_bin_kinetic(a, bin, s) : launch_bin_viscous(a, bin, s);
+  if (a.kinetic) return launch_bin_kinetic(a, bin, s);
+  return a.energy ? launch_bin_energy(a, bin, s) : launch_bin_viscous(a, bin, s);
 }
 int plain_scratch_bytes(int nf_max, int na_max);
 int plain_solve_one(rve_batch* b, int r, int out, const double* F, double tol, int max_iter, double* sigma,
@@ -80,6 +83,9 @@ int valid_options(const rve_options& o) {
     return fail(RVE_EINVAL, "damping_mode must be RVE_DAMP_VISCOUS or RVE_DAMP_KINETIC");
   if (o.damping_mode == RVE_DAMP_KINETIC && o.precision == RVE_PREC_PLAIN_F64)
     return fail(RVE_EINVAL, "kinetic damping runs on the batched precisions");
+  if (o.energy_check != 0 && o.energy_check != 1) return fail(RVE_EINVAL, "energy_check must be 0 or 1");
+  if (o.energy_check && (o.precision == RVE_PREC_PLAIN_F64 || o.damping_mode == RVE_DAMP_KINETIC))
+    return fail(RVE_EINVAL, "the energy balance runs on the batched precisions with viscous damping");
   if (o.threads != 0 && o.threads != 64 && o.threads != 128 && o.threads != 256 && o.threads != 512 &&
       o.threads != 1024)
     return fail(RVE_EINVAL, "threads must be 0, 64, 128, 256, 512 or 1024");
@@ -384,6 +390,10 @@ DrArgs<T> make_args(rve_batch* b, const double* F, double tol, int max_iter, dou
   a.kinetic = b->opt.damping_mode == RVE_DAMP_KINETIC ? 1 : 0;
   a.damping_scale = b->opt.damping_scale > 0.0 ? b->opt.damping_scale : DAMP_SCALE;
   a.sigma_tol = b->opt.sigma_tol;
+  a.wave_iters = 0;
+  a.resume = nullptr;
+  a.vel = nullptr;
+  a.energy = nullptr;
   return a;
 }
 
@@ -404,17 +414,29 @@ int order_after_last(rve_batch* b, cudaStream_t s) {
   return RVE_OK;
 }
 
+// Per-RVE energy records of the all-RVE solve (option energy_check).
+int energy_buffer(rve_batch* b, PathState& P, double** out) {
+  if (!P.d_energy) {
+    TRY(dalloc(b, reinterpret_cast<void**>(&P.d_energy), sizeof(double) * 6 * size_t(std::max<int64_t>(b->n_rve, 1))));
+    RVE_CUDA_TRY(cudaMemset(P.d_energy, 0, sizeof(double) * 6 * size_t(std::max<int64_t>(b->n_rve, 1))));
+  }
+  *out = P.d_energy;
+  return RVE_OK;
+}
+
 int solve_all(rve_batch* b, const double* F, double tol, int max_iter, double* sigma, int32_t* iters,
               int32_t* status, cudaStream_t s) {
   const int prec = b->opt.precision;
   if (prec == RVE_PREC_MIXED) {
     TRY(ensure_path<float>(b));
-    const DrArgs<float> a = make_args<float>(b, F, tol, max_iter, sigma, iters, status, b->pf.d_state, b->opt.warm_start);
+    DrArgs<float> a = make_args<float>(b, F, tol, max_iter, sigma, iters, status, b->pf.d_state, b->opt.warm_start);
+    if (b->opt.energy_check) TRY(energy_buffer(b, b->pf, &a.energy));
     return run_bins(b, b->pf.bins, a, s);
   }
   if (prec == RVE_PREC_BATCHED_F64) {
     TRY(ensure_path<double>(b));
-    const DrArgs<double> a = make_args<double>(b, F, tol, max_iter, sigma, iters, status, b->pd.d_state, b->opt.warm_start);
+    DrArgs<double> a = make_args<double>(b, F, tol, max_iter, sigma, iters, status, b->pd.d_state, b->opt.warm_start);
+    if (b->opt.energy_check) TRY(energy_buffer(b, b->pd, &a.energy));
     return run_bins(b, b->pd.bins, a, s);
   }
   TRY(ensure_path<double>(b));  // state buffer shared with the FP64 batched path
@@ -908,6 +930,12 @@ namespace rvegpu {
 int solve_subset(rve_batch* b, const int64_t* ids, int64_t m, const double* F, double tol, int32_t max_iter,
                  double* sigma, int32_t* iters, int32_t* status, cudaStream_t s, bool fork,
                  const SubsetBuffers* ext) {
+  return solve_items(b, ids, nullptr, m, F, tol, max_iter, sigma, iters, status, s, fork, ext, nullptr);
+}
+
+int solve_items(rve_batch* b, const int64_t* ids, const int32_t* outs, int64_t m, const double* F, double tol,
+                int32_t max_iter, double* sigma, int32_t* iters, int32_t* status, cudaStream_t s, bool fork,
+                const SubsetBuffers* ext, const WaveParams* wave) {
   if (!b) return fail(RVE_EINVAL, "null batch");
   if (m == 0) return RVE_OK;
   if (m < 0 || !ids || !F || !sigma) return fail(RVE_EINVAL, "bad subset arguments");
@@ -922,9 +950,10 @@ int solve_subset(rve_batch* b, const int64_t* ids, int64_t m, const double* F, d
   }
   const int prec = b->opt.precision;
   if (prec == RVE_PREC_PLAIN_F64) {
+    if (wave && wave->wave_iters > 0) return fail(RVE_EINVAL, "iteration-level waves need a batched precision");
     TRY(ensure_path<double>(b));
     for (int64_t k = 0; k < m; ++k)
-      TRY(plain_solve_one(b, int(ids[k]), int(k), F, tol, max_iter, sigma, iters, status, s));
+      TRY(plain_solve_one(b, int(ids[k]), outs ? outs[k] : int(k), F, tol, max_iter, sigma, iters, status, s));
     return RVE_OK;
   }
   const bool f32 = prec == RVE_PREC_MIXED;
@@ -943,7 +972,7 @@ int solve_subset(rve_batch* b, const int64_t* ids, int64_t m, const double* F, d
   for (int64_t k = 0; k < m; ++k) {
     const int r = int(ids[k]);
     Work w = P.work_of[r];
-    w.out = int32_t(k);
+    w.out = outs ? outs[k] : int32_t(k);
     bins[P.bin_of[r]].work.push_back(w);
   }
   for (Bin& x : bins)
@@ -988,11 +1017,26 @@ int solve_subset(rve_batch* b, const int64_t* ids, int64_t m, const double* F, d
   RVE_CUDA_TRY(cudaMemcpyAsync(buf.d_work, buf.h_stage, off * sizeof(Work), cudaMemcpyHostToDevice, s));
   if (!ext) RVE_CUDA_TRY(cudaEventRecord(b->ev_work, s));
   if (f32) {
-    const DrArgs<float> a = make_args<float>(b, F, tol, max_iter, sigma, iters, status, b->pf.d_state, b->opt.warm_start);
+    DrArgs<float> a = make_args<float>(b, F, tol, max_iter, sigma, iters, status, b->pf.d_state, b->opt.warm_start);
+    if (wave) {
+      a.wave_iters = wave->wave_iters;
+      a.resume = wave->resume;
+      a.vel = static_cast<float*>(wave->vel);
+    }
     return run_bins(b, bins, a, s, fork);
   }
-  const DrArgs<double> a = make_args<double>(b, F, tol, max_iter, sigma, iters, status, b->pd.d_state, b->opt.warm_start);
+  DrArgs<double> a = make_args<double>(b, F, tol, max_iter, sigma, iters, status, b->pd.d_state, b->opt.warm_start);
+  if (wave) {
+    a.wave_iters = wave->wave_iters;
+    a.resume = wave->resume;
+    a.vel = static_cast<double*>(wave->vel);
+  }
   return run_bins(b, bins, a, s, fork);
+}
+
+int ensure_batched_path(rve_batch* b) {
+  if (b->opt.precision == RVE_PREC_MIXED) return ensure_path<float>(b);
+  return ensure_path<double>(b);
 }
 }  // namespace rvegpu
 
@@ -1071,6 +1115,20 @@ int rve_last_kernel_ms(rve_batch* b, int32_t max, double* ms) {
     ms[k] = double(t);
   }
   return n;
+}
+
+int rve_energy(rve_batch* b, int32_t precision, double* energy, void* stream) {
+  if (!b || !energy) return fail(RVE_EINVAL, "batch and energy are required");
+  if (precision != RVE_PREC_MIXED && precision != RVE_PREC_BATCHED_F64)
+    return fail(RVE_EINVAL, "energy records exist on the batched precisions");
+  const PathState& P = precision == RVE_PREC_MIXED ? b->pf : b->pd;
+  if (!P.d_energy) return fail(RVE_EINVAL, "no energy records: solve with the option energy_check = 1 first");
+  TRY(set_device(b));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TRY(order_after_last(b, s));
+  RVE_CUDA_TRY(cudaMemcpyAsync(energy, P.d_energy, sizeof(double) * 6 * size_t(b->n_rve), cudaMemcpyDeviceToDevice, s));
+  RVE_CUDA_TRY(cudaEventRecord(b->ev_last, s));
+  return RVE_OK;
 }
 
 int rve_orientation(rve_batch* b, const double* F, int32_t precision, double* omega, void* stream) {

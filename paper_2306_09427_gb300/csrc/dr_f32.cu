@@ -3,6 +3,6 @@
 
 namespace rvegpu {
 int launch_bin_viscous(const DrArgs<float>& a, const Bin& bin, cudaStream_t s) {
-  return launch_bin_t<float, false>(a, bin, s);
+  return launch_bin_t<float, VAR_VISCOUS>(a, bin, s);
 }
 }  // namespace rvegpu

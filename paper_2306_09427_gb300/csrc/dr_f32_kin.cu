@@ -3,6 +3,6 @@
 
 namespace rvegpu {
 int launch_bin_kinetic(const DrArgs<float>& a, const Bin& bin, cudaStream_t s) {
-  return launch_bin_t<float, true>(a, bin, s);
+  return launch_bin_t<float, VAR_KINETIC>(a, bin, s);
 }
 }  // namespace rvegpu

@@ -3,6 +3,6 @@
 
 namespace rvegpu {
 int launch_bin_viscous(const DrArgs<double>& a, const Bin& bin, cudaStream_t s) {
-  return launch_bin_t<double, false>(a, bin, s);
+  return launch_bin_t<double, VAR_VISCOUS>(a, bin, s);
 }
 }  // namespace rvegpu

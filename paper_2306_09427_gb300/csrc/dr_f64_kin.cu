@@ -3,6 +3,6 @@
 
 namespace rvegpu {
 int launch_bin_kinetic(const DrArgs<double>& a, const Bin& bin, cudaStream_t s) {
-  return launch_bin_t<double, true>(a, bin, s);
+  return launch_bin_t<double, VAR_KINETIC>(a, bin, s);
 }
 }  // namespace rvegpu

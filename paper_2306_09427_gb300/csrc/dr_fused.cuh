@@ -17,14 +17,14 @@
 //            a fixed CSR order, four entries per 8-byte load (runs padded
 //            with a zero slot); deterministic, no atomics (the paper's
 //            getInternalForces scatters with atomics, Sec. 4.3);
-//     check  every check_every iterations: ||f_free||_2 (per-thread and
-//            per-warp partials in T, summed across warps in FP64 by warp 0)
+//     check  every check_every iterations: ||f_free||_2 (products, per-thread,
+//            per-warp and cross-warp sums all in FP64)
 //            against max(tol R_aff, 1e-16 sum EA) and, with sigma_tol > 0,
 //            the estimated remaining stress error; damping re-estimated,
 //            c = s 2 sqrt(lambda) from the Rayleigh quotient lambda; thread 0
 //            takes these block-uniform decisions and publishes them;
 //     update m = MASS_COEF sbar_sum, v <- ((2-c) v + 2 f/m)/(2+c),
-//            |v| capped, h <- h + v (dt = 1); with KIN (kinetic damping)
+//            |v| capped, h <- h + v (dt = 1); with VAR_KINETIC (kinetic damping)
 //            c = 0 and a step past a kinetic-energy peak is taken back and
 //            the motion restarts from rest.
 //   finish   sigma = (sigma_bb + sum_e s_e d_e (x) d_e) / (det F V0) with
@@ -197,6 +197,31 @@ __device__ __forceinline__ double law_f64(double eps, double EA, double B) {
   return B > 0.0 ? (EA / B) * expm1(B * eps) : EA * eps;
 }
 
+// Stored energy of one fiber, w(l) = integral of N from L0 to l, by 8-point
+// Gauss-Legendre quadrature on [L0, l] (nodes and weights of Abramowitz and
+// Stegun, Table 25.4); N is smooth (the exponential of a quadratic in l), so
+// the rule is exact to the loop type's rounding over the strains of a
+// solve.  inv2L02 = 1/(2 L0^2), eab = EA/B (EA when B = 0).
+template <typename T>
+__device__ __forceinline__ T fiber_energy_gl8(T l, T inv2L02, T eab, T B) {
+  const T t[4] = {T(0.1834346424956498), T(0.5255324099163290), T(0.7966664774136267), T(0.9602898564975363)};
+  const T w[4] = {T(0.3626837833783620), T(0.3137066458778873), T(0.2223810344533745), T(0.1012285362903763)};
+  const T L0 = sqrt(T(0.5) / inv2L02);
+  const T mid = T(0.5) * (l + L0), half = T(0.5) * (l - L0);
+  T acc = T(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+      const T lk = mid + T(sgn) * half * t[k];
+      const T eps = (lk * lk) * inv2L02 - T(0.5);
+      const T N = B > T(0) ? eab * k_expm1(B * eps) : eab * eps;
+      acc += w[k] * N;
+    }
+  }
+  return half * acc;
+}
+
 // Accumulate a fiber's stress terms s d (x) d (o = s d) into FP64 partials
 // (xx yy zz yz xz xy), used by the stress-convergence test at checks.
 template <typename T, typename V4>
@@ -207,6 +232,191 @@ __device__ __forceinline__ void add_virial(double (&ps)[6], const V4& o, T Dx, T
   ps[3] += double(o.y * Dz);
   ps[4] += double(o.x * Dz);
   ps[5] += double(o.x * Dy);
+}
+
+// Fiber part of a rebase: FP64 chord g_e = F dX_e + h_ref,j - h_ref,i and
+// Green strain of every active fiber at the new reference state.  Out of
+// line: it runs once per REBASE_EVERY checks, and its FP64 temporaries then
+// do not add to the register pressure of the relaxation loop.
+template <typename T, typename V4>
+__device__ __noinline__ void rebase_fibers(const FibD* __restrict__ fa, int na, int tid, int nt, const double* sF,
+                                           const double* HR, V4* P0, const V4* P1) {
+  for (int e = tid; e < na; e += nt) {
+    const FibD q = fa[e];
+    const uint32_t ij = k_unpack_ij(P1[e].w);
+    const uint32_t i = ij & 0xffffu, j = ij >> 16;
+    const double gx = sF[0] * q.dx + sF[1] * q.dy + sF[2] * q.dz + (HR[3 * j + 0] - HR[3 * i + 0]);
+    const double gy = sF[3] * q.dx + sF[4] * q.dy + sF[5] * q.dz + (HR[3 * j + 1] - HR[3 * i + 1]);
+    const double gz = sF[6] * q.dx + sF[7] * q.dy + sF[8] * q.dz + (HR[3 * j + 2] - HR[3 * i + 2]);
+    V4 p0;
+    p0.x = T(gx);
+    p0.y = T(gy);
+    p0.z = T(gz);
+    p0.w = T((gx * gx + gy * gy + gz * gz - q.L0 * q.L0) * q.half_inv_L02);
+    P0[e] = p0;
+  }
+}
+
+// Block-uniform decisions of a convergence check, taken by warp 0 (lane 0
+// decides) from the per-warp FP64 partials in red (9 per warp: ||f||^2,
+// v.(f_new - f_old), v.M v, then the 6 stress components when the stress
+// test is on).  Publishes the outcome in *flag (-1: keep iterating, or the
+// final status) and, with adaptive damping, the new damping c in *c_sh and
+// its update factors in ab[0..1].  Out of line: it runs once per check
+// interval.
+template <typename T, int NW>
+__device__ __noinline__ void check_decide(const double* red, bool sig_test, int n_checks, int it, int it0,
+                                          bool have_pre, bool adaptive, int max_iter, double damping_scale,
+                                          double sigma_tol, int park_after, const double* thr,
+                                          double (*sig)[8], const double* bb, T* ab, double* c_sh, int* flag_out) {
+  const int lane = threadIdx.x & 31;
+  double v3[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) v3[k] = 0.0;
+  if (lane < NW) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v3[k] = red[lane * 9 + k];
+    if (sig_test) {
+#pragma unroll
+      for (int k = 3; k < 9; ++k) v3[k] = red[lane * 9 + k];
+    }
+  }
+#pragma unroll
+  for (int o = NW / 2; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v3[k] += __shfl_xor_sync(0xffffffffu, v3[k], o);
+    if (sig_test) {
+#pragma unroll
+      for (int k = 3; k < 9; ++k) v3[k] += __shfl_xor_sync(0xffffffffu, v3[k], o);
+    }
+  }
+  if (lane != 0) return;
+  int flag = -1;  // keep iterating; otherwise the final status
+  if (!(v3[0] < 1e300)) {  // NaN or Inf
+    flag = RVE_STATUS_NONFINITE;
+  } else {
+    bool sig_ok = true;
+    if (sig_test && v3[0] > thr[1]) {
+      // remaining stress error of a geometrically converging sequence, from
+      // the stress and residual SIG_WINDOW checks back (ring of records)
+      const double* prev = sig[(n_checks + 1) % (SIG_WINDOW + 1)];
+      double* next = sig[n_checks % (SIG_WINDOW + 1)];
+      const double r = sqrt(v3[0]);
+      double dn = 0.0, nn = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const double sg = v3[3 + k] + bb[2 * k] + bb[2 * k + 1];
+        const double wk2 = k < 3 ? 1.0 : 2.0;  // off-diagonal entries appear twice
+        dn += wk2 * (sg - prev[k]) * (sg - prev[k]);
+        nn += wk2 * sg * sg;
+        next[k] = sg;
+      }
+      sig_ok = false;
+      if (prev[7] != 0.0 && nn > 0.0) {
+        const double rho = fmin(r / prev[6], SIG_RHO_CAP);
+        sig_ok = sqrt(dn / nn) * rho / (1.0 - rho) <= sigma_tol;
+      }
+      next[6] = r;
+      next[7] = 1.0;
+    } else if (sig_test) {
+      sig[n_checks % (SIG_WINDOW + 1)][7] = 0.0;
+    }
+    if (v3[0] <= thr[0] && sig_ok) {
+      flag = RVE_STATUS_CONVERGED;
+    } else if (it >= max_iter) {
+      flag = RVE_STATUS_MAX_ITER;
+    } else {
+      if (adaptive && have_pre && v3[2] > 0.0) {
+        const double lam = -v3[1] / v3[2];
+        if (lam > 0.0) {
+          const double c = fmin(damping_scale * 2.0 * sqrt(lam), DAMP_C_MAX);
+          *c_sh = c;
+          ab[0] = T((2.0 - c) / (2.0 + c));
+          ab[1] = T(2.0 / (2.0 + c));
+        }
+      }
+      // end of a serving wave: park before the update of this iteration
+      if (park_after > 0 && it - it0 >= park_after) flag = RVE_STATUS_PARKED_INTERNAL;
+    }
+  }
+  *flag_out = flag;
+}
+
+// Compensated (Neumaier) FP64 sums of s d (x) d over this thread's active
+// fibers at the current state (P0 at h_ref, H holding the correction),
+// reduced over the warp; lane 0 writes the 6 (sum, compensation) pairs of
+// its warp to red[(warp * 6 + k) * 2 + {0, 1}].  Out of line: once per solve.
+template <typename T, typename V4>
+__device__ __noinline__ void fiber_stress_partials(const V4* P0, const V4* P1, const V4* H, int na, int tid, int nt,
+                                                   double* red) {
+  CSum s6[6];
+  for (int e = tid; e < na; e += nt) {
+    const V4 p0 = P0[e];
+    const V4 p1 = P1[e];
+    const uint32_t ij = k_unpack_ij(p1.w);
+    const V4 hi = H[ij & 0xffffu];
+    const V4 hj = H[ij >> 16];
+    T Dx, Dy, Dz, s, sbar;
+    fiber_force<T>(p0, p1, hi, hj, Dx, Dy, Dz, s, sbar);
+    const double sd = double(s), dx = double(Dx), dy = double(Dy), dz = double(Dz);
+    s6[0].add(sd * dx * dx);
+    s6[1].add(sd * dy * dy);
+    s6[2].add(sd * dz * dz);
+    s6[3].add(sd * dy * dz);
+    s6[4].add(sd * dx * dz);
+    s6[5].add(sd * dx * dy);
+  }
+  const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double s = s6[k].s, cc = s6[k].c;
+    warp_csum(s, cc);
+    if (lane == 0) {
+      red[(warp * 6 + k) * 2 + 0] = s;
+      red[(warp * 6 + k) * 2 + 1] = cc;
+    }
+  }
+}
+
+// Boundary-to-boundary fibers (fixed length under the affine BC): their
+// stress share as compensated per-warp partials in red (layout as
+// fiber_stress_partials) and their share of the affine force scale
+// sum N^2 (returned, this thread's fibers).  Out of line: once per solve.
+static __device__ __noinline__ double boundary_stress_partials(const FibD* __restrict__ fb, int nb, int tid, int nt,
+                                                        const double* sF, const double* sE, double* red) {
+  CSum sb6[6];
+  double raff2 = 0.0;
+  for (int e = tid; e < nb; e += nt) {
+    const FibD q = fb[e];
+    const double gx = sF[0] * q.dx + sF[1] * q.dy + sF[2] * q.dz;
+    const double gy = sF[3] * q.dx + sF[4] * q.dy + sF[5] * q.dz;
+    const double gz = sF[6] * q.dx + sF[7] * q.dy + sF[8] * q.dz;
+    const double ex = sE[0] * q.dx + sE[1] * q.dy + sE[2] * q.dz;
+    const double ey = sE[3] * q.dx + sE[4] * q.dy + sE[5] * q.dz;
+    const double ez = sE[6] * q.dx + sE[7] * q.dy + sE[8] * q.dz;
+    const double L02 = q.L0 * q.L0;
+    const double a = (q.dx * ex + q.dy * ey + q.dz * ez + 0.5 * (q.dx * q.dx + q.dy * q.dy + q.dz * q.dz - L02)) / L02;
+    const double N = law_f64(a, q.EA, q.B);
+    raff2 += N * N;
+    const double s = N / sqrt(gx * gx + gy * gy + gz * gz);
+    sb6[0].add(s * gx * gx);
+    sb6[1].add(s * gy * gy);
+    sb6[2].add(s * gz * gz);
+    sb6[3].add(s * gy * gz);
+    sb6[4].add(s * gx * gz);
+    sb6[5].add(s * gx * gy);
+  }
+  const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double s = sb6[k].s, cc = sb6[k].c;
+    warp_csum(s, cc);
+    if (lane == 0) {
+      red[(warp * 6 + k) * 2 + 0] = s;
+      red[(warp * 6 + k) * 2 + 1] = cc;
+    }
+  }
+  return raff2;
 }
 
 // Rebase (mixed-precision iterative refinement of the reference state).
@@ -262,26 +472,16 @@ __device__ __forceinline__ void rebase(const DrArgs<T>& A, const Work& wk, const
     H[nf] = z;
   }
   __syncthreads();
-  for (int e = tid; e < na; e += NT) {
-    const FibD q = A.fa[M.fa_off + e];
-    const uint32_t ij = k_unpack_ij(P1[e].w);
-    const uint32_t i = ij & 0xffffu, j = ij >> 16;
-    const double gx = sF[0] * q.dx + sF[1] * q.dy + sF[2] * q.dz + (HR[3 * j + 0] - HR[3 * i + 0]);
-    const double gy = sF[3] * q.dx + sF[4] * q.dy + sF[5] * q.dz + (HR[3 * j + 1] - HR[3 * i + 1]);
-    const double gz = sF[6] * q.dx + sF[7] * q.dy + sF[8] * q.dz + (HR[3 * j + 2] - HR[3 * i + 2]);
-    V4 p0;
-    p0.x = T(gx);
-    p0.y = T(gy);
-    p0.z = T(gz);
-    p0.w = T((gx * gx + gy * gy + gz * gz - q.L0 * q.L0) * q.half_inv_L02);
-    P0[e] = p0;
-  }
+  rebase_fibers<T, V4>(A.fa + M.fa_off, na, tid, NT, sF, HR, P0, P1);
   __syncthreads();
 }
 
-// KIN: kinetic damping (a separate instantiation, so that the viscous
-// default carries none of its code or registers).
-template <typename T, int NT, int NPT, int MODE, bool KIN>
+// VAR selects the loop variant, each its own instantiation so that the
+// viscous default carries none of the others' code or registers:
+// VAR_VISCOUS (adaptive or fixed viscous damping), VAR_KINETIC (kinetic
+// damping), VAR_ENERGY (viscous damping with Algorithm 2's optional energy
+// balance bookkeeping).
+template <typename T, int NT, int NPT, int MODE, int VAR>
 __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const DrArgs<T> A) {
   using V4 = typename Vec4<T>::t;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -293,8 +493,14 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
   // decisions of a check, published by thread 0: outcome and damping factors
   __shared__ int sFlag;
   __shared__ T sAB[2];
+  __shared__ double sC;  // damping coefficient in use (thread 0 decides it)
   // kinetic damping: per-warp kinetic-energy partials, double-buffered by iteration parity
   __shared__ T sKE[2][32];
+  // energy balance (VAR_ENERGY, thread 0): stored energy at the start, running
+  // FP64 totals of the damping and cap dissipation and the mass-change work,
+  // the last check's stored-energy change and kinetic energy, and the largest
+  // relative balance error seen
+  __shared__ double sEn[8];
 
   const Work wk = A.work[blockIdx.x];
   const RveMeta M = A.meta[wk.rve];
@@ -365,27 +571,8 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
     P1[e] = p1;
   }
   // boundary-to-boundary fibers: fixed length, stress share summed once
-  CSum sb6[6];
-  for (int e = tid; e < nb; e += NT) {
-    const FibD q = A.fb[M.fb_off + e];
-    const double gx = sF[0] * q.dx + sF[1] * q.dy + sF[2] * q.dz;
-    const double gy = sF[3] * q.dx + sF[4] * q.dy + sF[5] * q.dz;
-    const double gz = sF[6] * q.dx + sF[7] * q.dy + sF[8] * q.dz;
-    const double ex = sE[0] * q.dx + sE[1] * q.dy + sE[2] * q.dz;
-    const double ey = sE[3] * q.dx + sE[4] * q.dy + sE[5] * q.dz;
-    const double ez = sE[6] * q.dx + sE[7] * q.dy + sE[8] * q.dz;
-    const double L02 = q.L0 * q.L0;
-    const double a = (q.dx * ex + q.dy * ey + q.dz * ez + 0.5 * (q.dx * q.dx + q.dy * q.dy + q.dz * q.dz - L02)) / L02;
-    const double N = law_f64(a, q.EA, q.B);
-    raff2 += N * N;
-    const double s = N / sqrt(gx * gx + gy * gy + gz * gz);
-    sb6[0].add(s * gx * gx);
-    sb6[1].add(s * gy * gy);
-    sb6[2].add(s * gz * gz);
-    sb6[3].add(s * gy * gz);
-    sb6[4].add(s * gx * gz);
-    sb6[5].add(s * gx * gy);
-  }
+  // (per-warp compensated partials into red, combined below)
+  raff2 += boundary_stress_partials(A.fb + M.fb_off, nb, tid, NT, sF, sE, red);
   if constexpr (MODE == 0) {
     // runs are padded to 4 entries and start 8-byte aligned: copy 4 at a time
     uint2* csr_s = reinterpret_cast<uint2*>(const_cast<uint16_t*>(CSR));
@@ -398,8 +585,12 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
     z.x = z.y = z.z = z.w = T(0);
     SCR[na] = z;
   }
+  // a solve parked by the previous wave resumes from its record
+  ResumeRec rr{};
+  if (A.resume) rr = A.resume[wk.rve];
+  const bool resumed = A.resume != nullptr && rr.active != 0;
   // owned free nodes: correction d (= h - h_ref), velocity, step cap, CSR range
-  const bool warm = wk.kind == 1 || (A.warm_start && A.valid[wk.rve]);
+  const bool warm = resumed || wk.kind == 1 || (A.warm_start && A.valid[wk.rve]);
   T hx[NPT], hy[NPT], hz[NPT], vx[NPT], vy[NPT], vz[NPT];
   float cap[NPT];
   uint32_t cs[NPT];
@@ -413,20 +604,16 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
     if (a < nf) {
       cap[q] = A.ncap[M.node_off + a];
       cs[q] = A.ncsr[M.node_off + a];
+      if (resumed) {
+        const T* vv = A.vel + 4 * size_t(wk.state_off + a);
+        vx[q] = vv[0];
+        vy[q] = vv[1];
+        vz[q] = vv[2];
+      }
     }
   }
   // boundary-fiber stress share (compensated) -> sBB, then R_aff
   {
-    const int warp = tid >> 5, lane = tid & 31;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      double s = sb6[k].s, cc = sb6[k].c;
-      warp_csum(s, cc);
-      if (lane == 0) {
-        red[(warp * 6 + k) * 2 + 0] = s;
-        red[(warp * 6 + k) * 2 + 1] = cc;
-      }
-    }
     __syncthreads();
     if (tid < 6) {
       double s = 0.0, cc = 0.0;
@@ -458,19 +645,38 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
   // kinetic energy of a step is below the previous step's, that step went
   // past a peak: it is taken back and the motion restarts from rest.
   // Otherwise viscous damping, fixed or adaptive.
-  constexpr bool kinetic = KIN;
+  constexpr bool kinetic = VAR == VAR_KINETIC;
+  constexpr bool energy = VAR == VAR_ENERGY;
   const bool adaptive = !kinetic && !(A.damping > 0.0);
-  double c = kinetic ? 0.0 : (adaptive ? DAMP_C0 : A.damping);
+  double c = kinetic ? 0.0 : (adaptive ? DAMP_C0 : A.damping);  // start value; then sC
   T ke_prev = T(0);      // kinetic energy (sum m |v|^2) of the previous iteration's step
   bool kin_half = true;  // kinetic damping: the next step starts from rest (half step)
+  if (resumed) {
+    c = rr.c;
+    ke_prev = T(rr.ke_prev);
+    kin_half = rr.kin_half != 0;
+  }
   T alpha = T((2.0 - c) / (2.0 + c)), beta = T(2.0 / (2.0 + c));
   if (tid == 0) {
     sAB[0] = alpha;
     sAB[1] = beta;
+    sC = c;
   }
-  T pre = T(0), pm = T(0);  // thread partials from the iteration before a check
+  double pre = 0.0, pm = 0.0;  // thread partials (FP64) from the iteration before a check
   bool have_pre = false;
-  int it = 0, n_checks = 0;
+  // energy balance, per thread in T over a check interval (VAR_ENERGY), per
+  // step with the mean velocity vb = (v_old + v_new)/2 of the step taken:
+  // e_loss = f.vb - m (|v_new|^2 - |v_old|^2)/2, the kinetic energy the step
+  // lost to damping and the step cap; e_damp = c m |vb|^2, its viscous part;
+  // e_mass = (m - m_prev) |v_old|^2 / 2, the work of the mass change (the
+  // mass is re-evaluated every iteration)
+  T e_loss = T(0), e_damp = T(0), e_mass = T(0);
+  T m_prev[NPT];
+#pragma unroll
+  for (int q = 0; q < NPT; ++q) m_prev[q] = T(0);
+  if (energy && tid < 8) sEn[tid] = 0.0;
+  int it = resumed ? rr.it : 0, n_checks = resumed ? rr.n_checks : 0;
+  const int it0 = it;  // where this launch took the solve up (wave length)
   // stress-convergence test: below thr_tight the residual alone decides
   const bool sig_test = A.sigma_tol > 0.0;
   if (tid == 0) {
@@ -488,7 +694,6 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
       const bool check = (to_check == 0) || (it >= A.max_iter);
       to_check = (to_check == 0) ? K - 1 : to_check - 1;
       const bool want_sig = check && sig_test;
-      double ps[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
       // fiber phase (RVE_FIBER_UNROLL fibers per step: independent shared-memory loads overlap)
       for (int e = tid; e < na; e += RVE_FIBER_UNROLL * NT) {
         V4 p0[RVE_FIBER_UNROLL], p1[RVE_FIBER_UNROLL], hi[RVE_FIBER_UNROLL], hj[RVE_FIBER_UNROLL];
@@ -515,7 +720,6 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
             o.z = s * Dz;
             o.w = sbar;
             SCR[e + u * NT] = o;
-            if (want_sig) add_virial(ps, o, Dx, Dy, Dz);
           }
         }
       }
@@ -564,115 +768,113 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
       }
       bool do_rebase = false;
       if (check) {
-        // Per-thread and per-warp partials in the loop type T; the per-warp
-        // partials are summed in FP64 by warp 0, whose lane 0 takes every
-        // block-uniform decision once (convergence, damping) and publishes it
-        // in shared memory.  The stress-test sums stay in FP64 throughout.
-        T t3[3] = {T(0), T(0), pm};
+        // ||f||^2, v.(f_new - f_old) and v.M v: every product and partial sum
+        // in FP64 (per thread, per warp, across warps); warp 0 finishes the
+        // cross-warp sum and its lane 0 takes every block-uniform decision
+        // once (convergence, damping) and publishes it in shared memory.
+        double t3[3] = {0.0, 0.0, pm};
 #pragma unroll
         for (int q = 0; q < NPT; ++q) {
           if (tid + q * NT < nf) {
-            t3[0] += fx[q] * fx[q] + fy[q] * fy[q] + fz[q] * fz[q];
-            t3[1] += vx[q] * fx[q] + vy[q] * fy[q] + vz[q] * fz[q];
+            const double gx = double(fx[q]), gy = double(fy[q]), gz = double(fz[q]);
+            t3[0] += gx * gx + gy * gy + gz * gz;
+            t3[1] += double(vx[q]) * gx + double(vy[q]) * gy + double(vz[q]) * gz;
           }
         }
         t3[1] -= pre;
+        // stress-convergence test: the fiber stress sum at this iterate, in a
+        // pass of its own (the fiber loop keeps no FP64 partials live)
+        double ps[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        if (want_sig) {
+          for (int e = tid; e < na; e += NT) {
+            T Dx, Dy, Dz, sv, sbar;
+            const V4 p1 = P1[e];
+            const uint32_t ij = k_unpack_ij(p1.w);
+            fiber_force<T>(P0[e], p1, H[ij & 0xffffu], H[ij >> 16], Dx, Dy, Dz, sv, sbar);
+            V4 o;
+            o.x = sv * Dx;
+            o.y = sv * Dy;
+            o.z = sv * Dz;
+            o.w = sbar;
+            add_virial(ps, o, Dx, Dy, Dz);
+          }
+        }
         const int warp = tid >> 5, lane = tid & 31;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) t3[k] = warp_sum_t(t3[k]);
+        for (int k = 0; k < 3; ++k) t3[k] = warp_sum(t3[k]);
         if (sig_test) {
 #pragma unroll
           for (int k = 0; k < 6; ++k) ps[k] = warp_sum(ps[k]);
         }
         if (lane == 0) {
 #pragma unroll
-          for (int k = 0; k < 3; ++k) red[warp * 9 + k] = double(t3[k]);
+          for (int k = 0; k < 3; ++k) red[warp * 9 + k] = t3[k];
           if (sig_test) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) red[warp * 9 + 3 + k] = ps[k];
           }
         }
         __syncthreads();
-        if (warp == 0) {
-          constexpr int NW = NT / 32;
-          double v3[9];
-#pragma unroll
-          for (int k = 0; k < 9; ++k) v3[k] = 0.0;
-          if (lane < NW) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) v3[k] = red[lane * 9 + k];
-            if (sig_test) {
-#pragma unroll
-              for (int k = 3; k < 9; ++k) v3[k] = red[lane * 9 + k];
-            }
-          }
-#pragma unroll
-          for (int o = NW / 2; o > 0; o >>= 1) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) v3[k] += __shfl_xor_sync(0xffffffffu, v3[k], o);
-            if (sig_test) {
-#pragma unroll
-              for (int k = 3; k < 9; ++k) v3[k] += __shfl_xor_sync(0xffffffffu, v3[k], o);
-            }
-          }
-          if (lane == 0) {
-            int flag = -1;  // keep iterating; otherwise the final status
-            if (!(v3[0] < 1e300)) {  // NaN or Inf
-              flag = RVE_STATUS_NONFINITE;
-            } else {
-              bool sig_ok = true;
-              if (sig_test && v3[0] > sThr[1]) {
-                // remaining stress error of a geometrically converging sequence, from
-                // the stress and residual SIG_WINDOW checks back (ring of records)
-                const double* prev = sSig[(n_checks + 1) % (SIG_WINDOW + 1)];
-                double* next = sSig[n_checks % (SIG_WINDOW + 1)];
-                const double r = sqrt(v3[0]);
-                double dn = 0.0, nn = 0.0;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                  const double sg = v3[3 + k] + sBB[2 * k] + sBB[2 * k + 1];
-                  const double wk2 = k < 3 ? 1.0 : 2.0;  // off-diagonal entries appear twice
-                  dn += wk2 * (sg - prev[k]) * (sg - prev[k]);
-                  nn += wk2 * sg * sg;
-                  next[k] = sg;
-                }
-                sig_ok = false;
-                if (prev[7] != 0.0 && nn > 0.0) {
-                  const double rho = fmin(r / prev[6], SIG_RHO_CAP);
-                  sig_ok = sqrt(dn / nn) * rho / (1.0 - rho) <= A.sigma_tol;
-                }
-                next[6] = r;
-                next[7] = 1.0;
-              } else if (sig_test) {
-                sSig[n_checks % (SIG_WINDOW + 1)][7] = 0.0;
-              }
-              if (v3[0] <= sThr[0] && sig_ok) {
-                flag = RVE_STATUS_CONVERGED;
-              } else if (it >= A.max_iter) {
-                flag = RVE_STATUS_MAX_ITER;
-              } else if (adaptive && have_pre && v3[2] > 0.0) {
-                const double lam = -v3[1] / v3[2];
-                if (lam > 0.0) {
-                  c = fmin(A.damping_scale * 2.0 * sqrt(lam), DAMP_C_MAX);
-                  sAB[0] = T((2.0 - c) / (2.0 + c));
-                  sAB[1] = T(2.0 / (2.0 + c));
-                }
-              }
-            }
-            sFlag = flag;
-          }
-        }
+        if (warp == 0)
+          check_decide<T, NT / 32>(red, sig_test, n_checks, it, it0, have_pre, adaptive, A.max_iter, A.damping_scale,
+                                   A.sigma_tol, A.resume ? A.wave_iters : 0, sThr, sSig, sBB, sAB, &sC, &sFlag);
         __syncthreads();
         const int flag = sFlag;
+        if constexpr (energy) {
+          // Energy balance at this iterate x^n (Belytschko's check; three
+          // further sums of the state, as Algorithm 2 notes): the exact stored
+          // energy W of the active fibers (boundary-to-boundary fibers keep
+          // their length), the kinetic energy K of the last half step, the
+          // losses and mass work summed over the steps.  Along the trajectory
+          // -sum f.vb - v_old.f^n / 2 is the trapezoidal rule of the force
+          // work, and K + L - M equals it exactly (L = sum e_loss, M = sum
+          // e_mass), so the residual dW + K + L - M + v_old.f^n / 2 is the
+          // quadrature error of the central difference's steps against the
+          // exact energy change dW: the time-integration error the check
+          // exists to expose.
+          double ev[6] = {double(e_loss), double(e_damp), double(e_mass), 0.0, 0.0, 0.0};
+#pragma unroll
+          for (int q = 0; q < NPT; ++q) {
+            if (tid + q * NT < nf) {
+              ev[3] += 0.5 * double(m_prev[q]) * double(vx[q] * vx[q] + vy[q] * vy[q] + vz[q] * vz[q]);
+              ev[4] += 0.5 * double(vx[q] * fx[q] + vy[q] * fy[q] + vz[q] * fz[q]);
+            }
+          }
+          for (int e = tid; e < na; e += NT) {
+            const V4 p0 = P0[e], p1 = P1[e];
+            const uint32_t ij = k_unpack_ij(p1.w);
+            const V4 hi = H[ij & 0xffffu], hj = H[ij >> 16];
+            const T dx = p0.x + (hj.x - hi.x), dy = p0.y + (hj.y - hi.y), dz = p0.z + (hj.z - hi.z);
+            ev[5] += double(fiber_energy_gl8<T>(sqrt(dx * dx + dy * dy + dz * dz), p1.x, p1.y, p1.z));
+          }
+          block_allreduce<NT, 6>(ev, red);
+          if (tid == 0) {
+            sEn[1] += ev[0];  // L
+            sEn[2] += ev[1];  // D
+            sEn[3] += ev[2];  // M
+            if (n_checks == 0) sEn[0] = ev[5];  // stored energy at the start state
+            const double dW = ev[5] - sEn[0], K = ev[3];
+            sEn[4] = dW;
+            sEn[5] = K;
+            const double scale = fmax(fmax(fabs(dW), K), sEn[1]);
+            if (scale > 1e-300) sEn[6] = fmax(sEn[6], fabs(dW + K + sEn[1] - sEn[3] + ev[4]) / scale);
+          }
+          e_loss = e_damp = e_mass = T(0);
+          __syncthreads();  // red is free again
+        }
         if (flag == RVE_STATUS_NONFINITE || flag == RVE_STATUS_CONVERGED) {
           status = flag;
           break;
         }
         if (flag == RVE_STATUS_MAX_ITER) break;  // status is already RVE_STATUS_MAX_ITER
+        if (flag == RVE_STATUS_PARKED_INTERNAL) {
+          status = flag;
+          break;
+        }
         alpha = sAB[0];
         beta = sAB[1];
-        pre = T(0);
-        pm = T(0);
+        pre = 0.0;
+        pm = 0.0;
         have_pre = false;
         ++n_checks;
         do_rebase = std::is_same<T, float>::value && (n_checks % REBASE_EVERY == 0);
@@ -725,6 +927,15 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
               nvy *= sc;
               nvz *= sc;
             }
+            if constexpr (energy) {
+              const T cc = T(2) * (T(1) - alpha) / (T(1) + alpha);
+              const T bx = T(0.5) * (vx[q] + nvx), by = T(0.5) * (vy[q] + nvy), bz = T(0.5) * (vz[q] + nvz);
+              const T v2 = vx[q] * vx[q] + vy[q] * vy[q] + vz[q] * vz[q];
+              e_loss += (bx * fx[q] + by * fy[q] + bz * fz[q]) - T(0.5) * m * (nvx * nvx + nvy * nvy + nvz * nvz - v2);
+              e_damp += cc * m * (bx * bx + by * by + bz * bz);
+              e_mass += T(0.5) * (m - m_prev[q]) * v2;
+              m_prev[q] = m;
+            }
             hx[q] += nvx;
             hy[q] += nvy;
             hz[q] += nvz;
@@ -739,8 +950,9 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
           h4.w = T(0);
           H[a] = h4;
           if (pre_it) {
-            pre += nvx * fx[q] + nvy * fy[q] + nvz * fz[q];
-            pm += m * (nvx * nvx + nvy * nvy + nvz * nvz);
+            const double wx = double(nvx), wy = double(nvy), wz = double(nvz);
+            pre += wx * double(fx[q]) + wy * double(fy[q]) + wz * double(fz[q]);
+            pm += double(m) * (wx * wx + wy * wy + wz * wz);
           }
           if (kinetic) ke_t += m * (nvx * nvx + nvy * nvy + nvz * nvz);
         }
@@ -759,35 +971,43 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
     }
   }
 
-  // ---- stress: active fibers at the final state (P0 at h_ref, H holds d)
-  CSum s6[6];
-  for (int e = tid; e < na; e += NT) {
-    const V4 p0 = P0[e];
-    const V4 p1 = P1[e];
-    const uint32_t ij = k_unpack_ij(p1.w);
-    const V4 hi = H[ij & 0xffffu];
-    const V4 hj = H[ij >> 16];
-    T Dx, Dy, Dz, s, sbar;
-    fiber_force<T>(p0, p1, hi, hj, Dx, Dy, Dz, s, sbar);
-    const double sd = double(s), dx = double(Dx), dy = double(Dy), dz = double(Dz);
-    s6[0].add(sd * dx * dx);
-    s6[1].add(sd * dy * dy);
-    s6[2].add(sd * dz * dz);
-    s6[3].add(sd * dy * dz);
-    s6[4].add(sd * dx * dz);
-    s6[5].add(sd * dx * dy);
-  }
-  __syncthreads();  // red free (last allreduce read before the previous barrier)
-  const int warp = tid >> 5, lane = tid & 31;
+  if (status == RVE_STATUS_PARKED_INTERNAL) {
+    // park: h = h_ref + d into the state, the velocity and the loop scalars
+    // beside it; the next wave resumes from here (no stress yet)
+    double* st = A.state + 4 * size_t(wk.state_off);
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    double s = s6[k].s, cc = s6[k].c;
-    warp_csum(s, cc);
-    if (lane == 0) {
-      red[(warp * 6 + k) * 2 + 0] = s;
-      red[(warp * 6 + k) * 2 + 1] = cc;
+    for (int q = 0; q < NPT; ++q) {
+      const int a = tid + q * NT;
+      if (a < nf) {
+        st[4 * a + 0] += double(hx[q]);
+        st[4 * a + 1] += double(hy[q]);
+        st[4 * a + 2] += double(hz[q]);
+        T* vv = A.vel + 4 * size_t(wk.state_off + a);
+        vv[0] = vx[q];
+        vv[1] = vy[q];
+        vv[2] = vz[q];
+        vv[3] = T(0);
+      }
     }
+    if (tid == 0) {
+      ResumeRec r;
+      r.it = it;
+      r.n_checks = n_checks;
+      r.c = sC;
+      r.ke_prev = float(ke_prev);
+      r.kin_half = kin_half ? 1 : 0;
+      r.active = 1;
+      r.pad = 0;
+      A.resume[wk.rve] = r;
+      if (A.iters) A.iters[wk.out] = it;
+      if (A.status) A.status[wk.out] = status;
+    }
+    return;
   }
+
+  // ---- stress: active fibers at the final state (P0 at h_ref, H holds d)
+  __syncthreads();  // red free (last allreduce read before the previous barrier)
+  fiber_stress_partials<T, V4>(P0, P1, H, na, tid, NT, red);
   __syncthreads();
   if (tid < 6) {
     double s = sBB[2 * tid], cc = sBB[2 * tid + 1];
@@ -826,6 +1046,16 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
     if (wk.kind == 0) {
       A.valid[wk.rve] = (st == RVE_STATUS_NONFINITE) ? 0 : 1;  // never warm-start from NaN
       A.last_iters[wk.rve] = it;
+    }
+    if (A.resume) A.resume[wk.rve].active = 0;  // the next request starts afresh
+    if (energy && A.energy) {
+      double* E = A.energy + 6 * size_t(wk.out);
+      E[0] = sEn[4];           // stored-energy change from the start state
+      E[1] = sEn[5];           // kinetic energy at the last check
+      E[2] = sEn[2];           // viscous damping dissipation
+      E[3] = sEn[1] - sEn[2];  // further loss (step cap)
+      E[4] = sEn[3];           // work of the mass changes
+      E[5] = sEn[6];           // largest relative balance error over the checks
     }
     if (A.iters) A.iters[wk.out] = it;
     if (A.status) A.status[wk.out] = st;

@@ -8,9 +8,9 @@
 
 namespace rvegpu {
 
-template <typename T, int NT, int NPT, int MODE, bool KIN>
+template <typename T, int NT, int NPT, int MODE, int VAR>
 int launch_variant(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
-  auto fn = dr_fused_kernel<T, NT, NPT, MODE, KIN>;
+  auto fn = dr_fused_kernel<T, NT, NPT, MODE, VAR>;
   // largest dynamic shared memory opted in so far, per device ordinal; the
   // check and the attribute call stay together under one lock, so no thread
   // launches on a size another thread has recorded but not yet set
@@ -34,39 +34,39 @@ int launch_variant(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
   return RVE_OK;
 }
 
-template <typename T, int NT, int NPT, bool KIN>
+template <typename T, int NT, int NPT, int VAR>
 int launch_mode(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
   switch (bin.mode) {
-    case 0: return launch_variant<T, NT, NPT, 0, KIN>(a, bin, s);
+    case 0: return launch_variant<T, NT, NPT, 0, VAR>(a, bin, s);
     case 1:
-      if constexpr (NT >= 512 && NPT >= 2) return launch_variant<T, NT, NPT, 1, KIN>(a, bin, s);
+      if constexpr (NT >= 512 && NPT >= 2) return launch_variant<T, NT, NPT, 1, VAR>(a, bin, s);
       break;
     case 2:
-      if constexpr (NT >= 512 && NPT >= 2) return launch_variant<T, NT, NPT, 2, KIN>(a, bin, s);
+      if constexpr (NT >= 512 && NPT >= 2) return launch_variant<T, NT, NPT, 2, VAR>(a, bin, s);
       break;
   }
   return fail(RVE_EINVAL, "no kernel variant for this bin");
 }
 
-template <typename T, int NT, bool KIN>
+template <typename T, int NT, int VAR>
 int launch_npt(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
   switch (bin.npt) {
-    case 1: return launch_mode<T, NT, 1, KIN>(a, bin, s);
-    case 2: return launch_mode<T, NT, 2, KIN>(a, bin, s);
-    case 4: return launch_mode<T, NT, 4, KIN>(a, bin, s);
+    case 1: return launch_mode<T, NT, 1, VAR>(a, bin, s);
+    case 2: return launch_mode<T, NT, 2, VAR>(a, bin, s);
+    case 4: return launch_mode<T, NT, 4, VAR>(a, bin, s);
   }
   return fail(RVE_EINVAL, "nodes per thread must be 1, 2 or 4");
 }
 
-template <typename T, bool KIN>
+template <typename T, int VAR>
 int launch_bin_t(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
   if (bin.n == 0) return RVE_OK;
   switch (bin.nt) {
-    case 64: return launch_npt<T, 64, KIN>(a, bin, s);
-    case 128: return launch_npt<T, 128, KIN>(a, bin, s);
-    case 256: return launch_npt<T, 256, KIN>(a, bin, s);
-    case 512: return launch_npt<T, 512, KIN>(a, bin, s);
-    case 1024: return launch_npt<T, 1024, KIN>(a, bin, s);
+    case 64: return launch_npt<T, 64, VAR>(a, bin, s);
+    case 128: return launch_npt<T, 128, VAR>(a, bin, s);
+    case 256: return launch_npt<T, 256, VAR>(a, bin, s);
+    case 512: return launch_npt<T, 512, VAR>(a, bin, s);
+    case 1024: return launch_npt<T, 1024, VAR>(a, bin, s);
   }
   return fail(RVE_EINVAL, "threads per CTA must be 64, 128, 256, 512 or 1024");
 }

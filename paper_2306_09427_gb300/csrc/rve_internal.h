@@ -54,6 +54,24 @@ struct Work {
   int32_t pad;
 };
 
+// Loop state of a solve parked between the launches of an iteration-level
+// serving wave (one per RVE; the velocity is kept per free node beside it).
+struct ResumeRec {
+  int32_t it;        // DR iterations done so far
+  int32_t n_checks;  // convergence checks done (rebase schedule)
+  double c;          // damping coefficient in use
+  float ke_prev;     // kinetic damping: kinetic energy of the last step
+  int32_t kin_half;  // kinetic damping: next step starts from rest
+  int32_t active;    // 1: parked, resume from this record; 0: start afresh
+  int32_t pad;
+};
+constexpr int RVE_STATUS_PARKED_INTERNAL = 4;  // == RVE_STATUS_RUNNING
+
+// Loop variants of the fused kernel (template parameter VAR).
+constexpr int VAR_VISCOUS = 0;
+constexpr int VAR_KINETIC = 1;
+constexpr int VAR_ENERGY = 2;
+
 // Dynamic-relaxation constants of the explicit update (Sec. 3.2: the
 // mass, damping and time step are fictitious and chosen for speed).
 //   lumped mass   m_i = MASS_GAMMA * (dt^2/4) * sum_e 2 max(k_e, |N_e|/l_e),
@@ -93,7 +111,7 @@ constexpr double SIG_RHO_CAP = 0.95;
 // streamed: H and SCR only when they fit, otherwise H and the FP64
 // reference copy.
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-inline size_t red_bytes(int nt) { return align_up(size_t(nt / 32) * 12 * sizeof(double) + 256, 16); }
+inline size_t red_bytes(int nt) { return align_up(size_t(nt / 32) * 12 * sizeof(double) + 256, 16); }  // >= 6 per warp + 32
 // The fiber-scratch region also holds the FP64 reference state (3 doubles
 // per node) during a rebase, so it is the larger of the two.
 template <typename T>
@@ -152,6 +170,14 @@ struct DrArgs {
   double sigma_tol;        // > 0: also require the estimated stress error <= sigma_tol
   int32_t kinetic;         // 1: kinetic damping (no viscous term, velocity reset after a kinetic-energy peak)
   double damping_scale;    // s in the adaptive damping c = s * 2 sqrt(lambda)
+  // iteration-level waves (serving): with wave_iters > 0 a solve stops at the
+  // first check at least wave_iters iterations after this launch took it up,
+  // parks (state h, velocity, ResumeRec) and reports RVE_STATUS_RUNNING; the
+  // next launch of the same RVE resumes it.  resume == nullptr: no parking.
+  int32_t wave_iters;
+  ResumeRec* resume;       // per RVE
+  T* vel;                  // 4 T per state node (velocity of a parked solve)
+  double* energy;          // non-null: energy-balance variant, 6 doubles per output index
 };
 
 }  // namespace rvegpu

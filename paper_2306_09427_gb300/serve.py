@@ -1,4 +1,5 @@
-"""Serving driver: Poisson stream of RVE solve requests through ``RveServer``.
+"""Serving driver: Poisson stream of RVE solve requests through ``RveServer``
+(iteration-level waves of WAVE_ITERS DR iterations by default).
 
 Requests arrive with exponential inter-arrival times (counter-based stream,
 reproducible), each naming an RVE of a resident pool and its deformation
@@ -42,9 +43,12 @@ def request_stream(n_pool: int, rate: float, duration: float, seed: int = 5):
     return t, rve, F.reshape(n, 9)
 
 
+WAVE_ITERS = 200  # DR iterations per wave (solves park and resume between waves)
+
+
 def run_poisson(batch: RveBatch, t_arr, rve, F, n_slots: int = 4, max_wave: int = 2048,
-                hbm_cap_bytes: float = 150e9) -> dict:
-    srv = RveServer(batch, n_slots=n_slots, max_wave=max_wave, hbm_cap_bytes=hbm_cap_bytes)
+                hbm_cap_bytes: float = 150e9, wave_iters: int = WAVE_ITERS) -> dict:
+    srv = RveServer(batch, n_slots=n_slots, max_wave=max_wave, hbm_cap_bytes=hbm_cap_bytes, wave_iters=wave_iters)
     n = t_arr.shape[0]
     done_t = np.full(n, np.nan)
     sigma = np.full((n, 9), np.nan)
@@ -76,7 +80,8 @@ def run_poisson(batch: RveBatch, t_arr, rve, F, n_slots: int = 4, max_wave: int 
     return {"requests": int(n), "wall_s": wall, "throughput": n / wall, "offered_rate": n / float(t_arr[-1]),
             "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
             "mean_iters": float(iters.mean()), "converged_frac": float((status == 0).mean()),
-            "waves": int(stats["waves"]), "sigma": sigma, "status": status, "latency_s": lat}
+            "waves": int(stats["waves"]), "wave_iters": wave_iters, "sigma": sigma, "status": status,
+            "latency_s": lat}
 
 
 def main():
@@ -87,11 +92,13 @@ def main():
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--max-wave", type=int, default=2048)
     ap.add_argument("--precision", type=int, default=RVE_PREC_MIXED, help="0 plain FP64 per RVE, 1 mixed, 2 FP64")
+    ap.add_argument("--wave-iters", type=int, default=WAVE_ITERS, help="DR iterations per wave (0: whole solves)")
     a = ap.parse_args()
     nets = pool_networks(a.pool)
     b = RveBatch(rvegen.pack(nets), precision=a.precision, warm_start=1)
     t, rve, F = request_stream(a.pool, a.rate, a.duration)
-    res = run_poisson(b, t, rve, F, n_slots=a.slots, max_wave=a.max_wave)
+    wave = a.wave_iters if a.precision != 0 else 0
+    res = run_poisson(b, t, rve, F, n_slots=a.slots, max_wave=a.max_wave, wave_iters=wave)
     out = {k: v for k, v in res.items() if not isinstance(v, np.ndarray)}
     out.update(pool=a.pool, slots=a.slots, max_wave=a.max_wave, precision=a.precision)
     print(json.dumps(out))

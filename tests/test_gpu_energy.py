@@ -1,0 +1,103 @@
+"""Energy balance of the relaxation (Algorithm 2's optional energy check,
+option energy_check) on the GPU against the oracle's stored energy.
+
+The kernel evaluates the stored energy of the active fibers at every check
+(8-point Gauss-Legendre of the axial force per fiber); its change from the
+start to the end state must equal the oracle's (16-point Gauss-Legendre,
+``oracle.fiber_law.fiber_energy``) at the GPU's own start and end
+positions.  The balance of that change with the kinetic energy, the damping
+and cap dissipation and the work of the fictitious mass changes measures
+the time-integration error of the damped central difference (large steps
+early in a solve); it is reported and bounded.  The energy variant must take
+the default kernel's iterates.
+"""
+import numpy as np
+import pytest
+
+import rvegen
+from oracle.network import prune
+from oracle.fiber_law import fiber_energy
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rve():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2306_09427_gb300 as rve
+    return rve
+
+
+def _F(F):
+    import torch
+    return torch.tensor(np.asarray(F).reshape(-1, 9), dtype=torch.float64, device="cuda:0")
+
+
+def _stored_energy(net, x):
+    kept, _ = prune(net.conn, net.is_boundary)
+    c = net.conn[kept]
+    l = np.linalg.norm(x[c[:, 1]] - x[c[:, 0]], axis=1)
+    return float(np.sum(fiber_energy(l, net.L0[kept], net.EA[kept], net.B[kept])))
+
+
+def _batch():
+    nets, Fs = [], []
+    for k in range(8):
+        st = rvegen.Stream(4200 + k)
+        nets.append(rvegen.grid_network(5 + k % 3, 0.6 + 0.05 * (k % 3), st, EA="lognormal" if k % 2 else 1.0,
+                                        B=[5.0, 10.0, 20.0][k % 3]))
+        Fs.append(rvegen.random_F(st))
+    return nets, np.stack(Fs)
+
+
+@pytest.mark.parametrize("precision,tol,bound", [("mixed", 1e-6, 1e-4), ("fp64", 1e-10, 1e-8)])
+def test_energy_balance_against_the_oracle_energy(rve, precision, tol, bound):
+    prec = rve.RVE_PREC_MIXED if precision == "mixed" else rve.RVE_PREC_BATCHED_F64
+    nets, Fs = _batch()
+    b = rve.RveBatch(rvegen.pack(nets), precision=prec, tol=tol, energy_check=1)
+    s, it, st = b.solve(_F(Fs))
+    E = b.energy()
+    s, it, st = s.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
+    assert (st == rve.RVE_STATUS_CONVERGED).all()
+    # the default kernel takes the same iterates
+    b0 = rve.RveBatch(rvegen.pack(nets), precision=prec, tol=tol)
+    s0, it0, _ = b0.solve(_F(Fs))
+    s0, it0 = s0.cpu().numpy(), it0.cpu().numpy()
+    assert np.array_equal(it, it0)
+    assert np.abs(s - s0).max() <= 1e-12 * np.abs(s0).max()
+    b0.close()
+    rows = []
+    for k, net in enumerate(nets):
+        x = b.positions(k, Fs[k], net.n_nodes, prec)
+        dW = _stored_energy(net, x) - _stored_energy(net, net.X @ Fs[k].T)
+        rows.append((k, int(it[k]), dW, *E[k]))
+    for r in rows:
+        print("RVE %d: %6d iterations, dW oracle %.8e, dW GPU %.8e (rel %.1e), K %.2e D %.4e C %.2e M %.2e, "
+              "balance max %.1e" % (r[0], r[1], r[2], r[3], abs(r[3] - r[2]) / abs(r[2]), *r[4:]))
+    for k, _, dW, dW_gpu, K, D, C, M, bal in rows:
+        assert dW < 0.0                                   # relaxation releases stored energy
+        assert abs(dW_gpu - dW) <= bound * abs(dW), (k, dW_gpu, dW)
+        assert K >= 0.0 and D >= 0.0 and C >= -1e-9 * abs(dW)
+        assert K <= 1e-6 * abs(dW)                        # at rest at the converged state
+        # the damped central difference's quadrature error of the energy change:
+        # a few percent with the large early steps of the relaxation
+        assert bal <= 0.2, (k, bal)
+    b.close()
+
+
+def test_energy_records_need_the_option(rve):
+    nets, Fs = _batch()
+    b = rve.RveBatch(rvegen.pack(nets[:2]), precision=rve.RVE_PREC_MIXED)
+    b.solve(_F(Fs[:2]))
+    with pytest.raises(rve.RveError):
+        b.energy()
+    with pytest.raises(rve.RveError):
+        rve.RveBatch(rvegen.pack(nets[:2]), precision=rve.RVE_PREC_PLAIN_F64, energy_check=1)
+    with pytest.raises(rve.RveError):
+        rve.RveBatch(rvegen.pack(nets[:2]), precision=rve.RVE_PREC_MIXED, energy_check=1,
+                     damping_mode=rve.RVE_DAMP_KINETIC)
+    b.close()

@@ -4,6 +4,11 @@ Bars (sigma, relative Frobenius error against the oracle):
   mixed precision (FP32 forces, FP64 sums)  <= 1e-4
   FP64 batched and plain FP64 paths         <= 1e-10 on the 6^3 RVE at
                                               R_rel 1e-13, <= 1e-8 elsewhere
+Where a network holds several stable equilibria, a stress that differs from
+the oracle's is accepted only as a verified other minimum (tests/parity.py:
+the oracle polishes the GPU's state to relative residual 1e-10 and finds a
+stable minimum, by a fixed-shift inertia test, whose stress is within the
+bound); each such case is printed with both energies.
 """
 import json
 import os
@@ -16,6 +21,7 @@ import pytest
 import rvegen
 from oracle.newton import solve, solve_network
 from tests import nets as tnets
+from tests.parity import classify, rel
 
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -45,34 +51,17 @@ def gpu_solve(rve, nets, F, precision, tol, max_iter=0, **opts):
     return out
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-
-def match_or_other_minimum(b, k, net, F, s_gpu, precision, bound, s_ref):
-    """Several stable equilibria can be correct (a sub-isostatic network can
-    hold more than one).  Same minimum as the oracle's cold solve: sigma
-    within bound.  Otherwise the GPU's final state must itself be a stable
-    equilibrium: the oracle polishes it (FP64 Newton from the GPU's
-    positions), checks stability, and sigma must match that minimum."""
-    if rel(s_gpu, s_ref) <= bound:
-        return "same"
-    x = b.positions(k, F, net.n_nodes, precision)
-    # a bounded polish: Newton converges fast from a state already near equilibrium
-    sol = solve_network(net, F, tol=1e-10, h0=x - net.X @ np.asarray(F).T, max_newton=30)
-    assert sol.stable, (k, sol.residual / sol.R_ref)
-    assert sol.residual <= 1e-4 * sol.R_ref, (k, sol.residual / sol.R_ref)
-    assert rel(s_gpu, sol.sigma) <= bound, (k, rel(s_gpu, sol.sigma))
-    print(f"  RVE {k}: other stable minimum, |sigma - oracle cold| = {rel(s_gpu, s_ref):.2e}, "
-          f"|sigma - oracle from GPU state| = {rel(s_gpu, sol.sigma):.2e}")
-    return "other"
-
-
 def _golden(name):
     path = os.path.join(HERE, "golden", f"oracle_{name}.json")
-    if not os.path.exists(path):
-        pytest.skip(f"{path} not generated")
-    return json.load(open(path))["rows"]
+    rows = json.load(open(path))["rows"]
+    # every stored row is a converged, stable oracle equilibrium at 1e-10
+    assert all(r["converged"] and r["stable"] for r in rows), path
+    return rows
+
+
+def _items(rows, nets, Fs, s):
+    return [dict(k=r["index"], net=nets[r["index"]], F=Fs[r["index"]], sigma=s[r["index"]],
+                 ref=np.array(r["sigma"]).reshape(3, 3), ref_energy=r["energy"]) for r in rows]
 
 
 # ----------------------------------------------------------------- config 1
@@ -157,11 +146,11 @@ def test_kinetic_damping_converges_to_same_state(rve, small_case, precision, tol
     # adaptive viscous damping on these sub-isostatic networks)
     assert conv.mean() >= 0.75, st
     assert ((st == rve.RVE_STATUS_CONVERGED) | (st == rve.RVE_STATUS_MAX_ITER)).all()
-    kinds = [match_or_other_minimum(b, k, nets[k], Fs[k], s[k], prec, bound, refs[k])
-             for k in range(len(nets)) if conv[k]]
+    items = [dict(k=k, net=nets[k], F=Fs[k], sigma=s[k], ref=refs[k]) for k in range(len(nets)) if conv[k]]
+    c = classify(b, prec, items, bound, f"kinetic {precision}")
     _, it_v, _ = gpu_solve(rve, nets, Fs, prec, tol)
-    print("kinetic (%s): %d/%d converged, median iterations %.0f (viscous adaptive %.0f); %d other minima"
-          % (precision, conv.sum(), len(nets), np.median(it), np.median(it_v), kinds.count("other")))
+    print("kinetic (%s): %d/%d converged, median iterations %.0f (viscous adaptive %.0f); %s"
+          % (precision, conv.sum(), len(nets), np.median(it), np.median(it_v), c))
     b.close()
 
 
@@ -173,22 +162,18 @@ BENCH_OPTS = dict(damping_scale=0.7)  # bench.py's options beyond the library de
 @pytest.mark.parametrize("opts", [{}, BENCH_OPTS], ids=["defaults", "bench"])
 def test_uniform_full_batch_sampled(rve, opts):
     """The bench's workload, with the library defaults and in the launch
-    configuration bench.py times."""
-    import torch
+    configuration bench.py times: 64 RVEs against stored oracle solves, and
+    all 1024 against a tight FP64 relaxation, every stress above 1e-4 of it
+    verified by the oracle as a stable minimum."""
     rows = _golden("uniform_10")
     nets, Fs = rvegen.config_uniform(1024)
     b = rve.RveBatch(rvegen.pack(nets), precision=rve.RVE_PREC_MIXED, **opts)
     s, it, st = b.solve(_F(Fs))
     s, st = s.cpu().numpy().reshape(-1, 3, 3), st.cpu().numpy()
     assert (st == rve.RVE_STATUS_CONVERGED).all()
-    kinds = []
-    for r in rows:
-        if r["converged"]:
-            k = r["index"]
-            kinds.append(match_or_other_minimum(b, k, nets[k], Fs[k], s[k], rve.RVE_PREC_MIXED, 1e-4,
-                                                np.array(r["sigma"]).reshape(3, 3)))
-    print("uniform sample vs oracle:", {k: kinds.count(k) for k in set(kinds)})
-    assert kinds.count("other") <= len(kinds) // 4
+    c = classify(b, rve.RVE_PREC_MIXED, _items(rows, nets, Fs, s), 1e-4, "uniform vs oracle")
+    print("uniform, 64 RVEs vs oracle:", c)
+    assert c["other"] <= 4
     # properties that hold at any size: symmetric stress, finite everywhere
     assert np.isfinite(s).all()
     assert np.abs(s - s.transpose(0, 2, 1)).max() <= 1e-12 * np.abs(s).max()
@@ -199,24 +184,24 @@ def test_uniform_full_batch_sampled(rve, opts):
     e = np.linalg.norm((s - s64).reshape(1024, -1), axis=1) / np.linalg.norm(s64.reshape(1024, -1), axis=1)
     print("uniform 1024: mixed vs FP64 DR sigma err max %.2e p99 %.2e n>1e-4 %d" % (e.max(), np.percentile(e, 99),
                                                                                   (e > 1e-4).sum()))
-    assert (e <= 1e-4).mean() >= 0.995
+    far = [dict(k=int(k), net=nets[k], F=Fs[k], sigma=s[k], ref=s64[k]) for k in np.nonzero(e > 1e-4)[0]]
+    c2 = classify(b, rve.RVE_PREC_MIXED, far, 1e-4, "uniform 1024 vs FP64 DR")
+    print("uniform 1024 vs FP64 DR:", {"within 1e-4": 1024 - len(far), **c2})
     b.close()
     b64.close()
 
 
 def test_uniform_fp64_sampled(rve):
-    rows = [r for r in _golden("uniform_10") if r["converged"]][:6]
+    rows = _golden("uniform_10")[:8]
     nets, Fs = rvegen.config_uniform(max(r["index"] for r in rows) + 1)
     # degenerate (floppy) RVEs need up to ~1e5 DR iterations to reach 1e-12
     b = rve.RveBatch(rvegen.pack(nets), precision=rve.RVE_PREC_BATCHED_F64, tol=1e-12, sigma_tol=0.0,
                      max_iter=2_000_000)
     s, it, st = b.solve(_F(Fs))
     s, st = s.cpu().numpy().reshape(-1, 3, 3), st.cpu().numpy()
-    for r in rows:
-        k = r["index"]
-        assert st[k] == rve.RVE_STATUS_CONVERGED, (k, int(it[k]))
-        match_or_other_minimum(b, k, nets[k], Fs[k], s[k], rve.RVE_PREC_BATCHED_F64, 1e-8,
-                               np.array(r["sigma"]).reshape(3, 3))
+    assert all(st[r["index"]] == rve.RVE_STATUS_CONVERGED for r in rows), (st, it)
+    c = classify(b, rve.RVE_PREC_BATCHED_F64, _items(rows, nets, Fs, s), 1e-8, "uniform fp64")
+    print("uniform FP64, 8 RVEs vs oracle:", c)
     b.close()
 
 
@@ -233,17 +218,41 @@ def test_uneven_batch(rve):
         s, it, st = b.solve(_F(Fs))
         s, st, it = s.cpu().numpy().reshape(-1, 3, 3), st.cpu().numpy(), it.cpu().numpy()
         t1 = time.perf_counter()
-        kinds = []
-        for r in rows:
-            if not r["converged"]:
-                continue
-            k = r["index"]
-            assert st[k] == rve.RVE_STATUS_CONVERGED, (prec, k)
-            kinds.append(match_or_other_minimum(b, k, nets[k], Fs[k], s[k], prec, bound,
-                                                np.array(r["sigma"]).reshape(3, 3)))
-        print("uneven precision", prec, kw, {k: kinds.count(k) for k in set(kinds)},
+        assert (st[:n] == rve.RVE_STATUS_CONVERGED).all(), (prec, np.nonzero(st != 0))
+        c = classify(b, prec, _items(rows, nets, Fs, s), bound, f"uneven {prec} {kw}")
+        print("uneven precision", prec, kw, c,
               "solve %.1f s (max %d iterations), oracle checks %.1f s" % (t1 - t0, it.max(), time.perf_counter() - t1))
-        assert kinds.count("other") <= len(kinds) // 2
+        assert c["other"] <= (6 if prec == rve.RVE_PREC_MIXED else 16)
+        b.close()
+
+
+def test_fe2_strip_rves_along_the_load_path(rve):
+    """Config 4's RVEs (8^3, p = 0.6) stepped through the strip's uniaxial
+    load path with the state kept on the device between steps (warm start),
+    against the oracle stepped the same way."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("mk", os.path.join(HERE, "golden", "make_golden.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    rows = _golden("fe2_8")
+    idx = sorted({r["index"] for r in rows})
+    nets = [mk.fe2_network(i) for i in idx]
+    for prec, tol, bound in ((rve.RVE_PREC_MIXED, 3e-7, 1e-4), (rve.RVE_PREC_BATCHED_F64, 1e-10, 1e-6)):
+        b = rve.RveBatch(rvegen.pack(nets), precision=prec, tol=tol, warm_start=1, max_iter=2_000_000)
+        tot = {"same": 0, "other": 0}
+        for k in range(1, mk.FE2_STEPS + 1):
+            F = mk.fe2_F(k)
+            Fs = np.repeat(F[None], len(nets), 0)
+            s, it, st = b.solve(_F(Fs))
+            s, st = s.cpu().numpy().reshape(-1, 3, 3), st.cpu().numpy()
+            assert (st == rve.RVE_STATUS_CONVERGED).all()
+            step = [r for r in rows if r["step"] == k]
+            items = [dict(k=j, net=nets[j], F=F, sigma=s[j], ref=np.array(r["sigma"]).reshape(3, 3),
+                          ref_energy=r["energy"]) for j, r in enumerate(step)]
+            c = classify(b, prec, items, bound, f"fe2 step {k} prec {prec}")
+            tot["same"] += c["same"]
+            tot["other"] += c["other"]
+        print("fe2 strip RVEs along the load path, precision", prec, tot)
         b.close()
 
 
