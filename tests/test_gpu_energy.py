@@ -81,7 +81,7 @@ def test_energy_balance_against_the_oracle_energy(rve, precision, tol, bound):
     for k, _, dW, dW_gpu, K, D, C, M, bal in rows:
         assert dW < 0.0                                   # relaxation releases stored energy
         assert abs(dW_gpu - dW) <= bound * abs(dW), (k, dW_gpu, dW)
-        assert K >= 0.0 and D >= 0.0 and C >= -1e-9 * abs(dW)
+        assert K >= 0.0 and D >= 0.0 and C >= -1e-6 * abs(dW)    # C >= 0 up to FP32 rounding of its sum
         assert K <= 1e-6 * abs(dW)                        # at rest at the converged state
         # the damped central difference's quadrature error of the energy change:
         # a few percent with the large early steps of the relaxation
