@@ -396,6 +396,19 @@ int rve_get_positions(rve_batch* b, int64_t r, const double* F, int32_t precisio
                       double* x_out);
 
 /*
+ * Set the state of RVE r on the given batched precision's path from node
+ * positions (HOST, 3 doubles per node in the reference node order, as
+ * rve_get_positions returns them) under the deformation gradient F (HOST, 9
+ * doubles): the fluctuation of every kept free node becomes x - F X and the
+ * state is marked valid, so the next solve with warm_start = 1 starts there
+ * (a saved state restored, or a relaxation continued on another path).
+ * Boundary and pruned nodes are ignored.  Synchronous.  RVE_EINVAL for an
+ * index out of range or the plain precision (which shares the FP64 state:
+ * use RVE_PREC_BATCHED_F64).
+ */
+int rve_set_positions(rve_batch* b, int64_t r, const double* F, int32_t precision, const double* x);
+
+/*
  * Continuous-batching request loop (serving) over a resident pool of RVEs.
  * The paper's RVE batch manager (Sec. 4.3) hands one batched solve per
  * macroscale iteration to the GPU; the server instead takes single requests

@@ -9,7 +9,7 @@ from ._lib import (RVE_DAMP_KINETIC, RVE_DAMP_VISCOUS, RVE_EADMIT, RVE_ECUDA, RV
                    RVE_PREC_MIXED, RVE_PREC_PLAIN_F64, RVE_STATUS_CONVERGED, RVE_STATUS_EMPTY,
                    RVE_STATUS_MAX_ITER, RVE_STATUS_NONFINITE, RVE_STATUS_RUNNING, RveBatch, RveError, RveServer, lib, lib_path,
                    rve_batch_create, rve_batch_destroy, rve_batch_get_info, rve_batch_get_sizes,
-                   rve_get_positions, rve_last_error, rve_options_default, rve_reset_state,
+                   rve_get_positions, rve_set_positions, rve_last_error, rve_options_default, rve_reset_state,
                    rve_set_options, rve_solve, rve_solve_host, rve_solve_plain_noalloc, rve_solve_subset,
                    rve_tangent, RVE_NOALLOC_MAX_ACTIVE_FIBERS, RVE_NOALLOC_MAX_FREE_NODES,
                    rve_server_create, rve_server_destroy, rve_server_drain, rve_server_get_stats,

@@ -61,6 +61,7 @@ rve_reset_state = _sig("rve_reset_state", C.c_int, [_P, _P, _I64])
 rve_batch_get_info = _sig("rve_batch_get_info", C.c_int, [_P, C.POINTER(rve_batch_info)])
 rve_batch_get_sizes = _sig("rve_batch_get_sizes", C.c_int, [_P, _P, _P, _P])
 rve_get_positions = _sig("rve_get_positions", C.c_int, [_P, _I64, _P, _I32, _P])
+rve_set_positions = _sig("rve_set_positions", C.c_int, [_P, _I64, _P, _I32, _P])
 
 
 class rve_bin_info(C.Structure):
@@ -320,6 +321,12 @@ class RveBatch:
         prec = self.opt.precision if precision is None else precision
         _check(rve_get_positions(self.h, r, _ptr(F), prec, _ptr(x)), "rve_get_positions")
         return x
+
+    def set_positions(self, r: int, F, x, precision: int | None = None) -> None:
+        F = np.ascontiguousarray(F, np.float64).reshape(9)
+        x = np.ascontiguousarray(x, np.float64)
+        prec = self.opt.precision if precision is None else precision
+        _check(rve_set_positions(self.h, r, _ptr(F), prec, _ptr(x)), "rve_set_positions")
 
 
 class RveServer:

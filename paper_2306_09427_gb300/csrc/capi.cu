@@ -1280,6 +1280,34 @@ int rve_get_positions(rve_batch* b, int64_t r, const double* F, int32_t precisio
   return RVE_OK;
 }
 
+int rve_set_positions(rve_batch* b, int64_t r, const double* F, int32_t precision, const double* x) {
+  if (!b || !F || !x) return fail(RVE_EINVAL, "null argument");
+  if (r < 0 || r >= b->n_rve) return fail(RVE_EINVAL, "RVE index out of range");
+  if (precision != RVE_PREC_MIXED && precision != RVE_PREC_BATCHED_F64)
+    return fail(RVE_EINVAL, "set positions on a batched precision (the plain path shares the FP64 state)");
+  TRY(set_device(b));
+  if (precision == RVE_PREC_MIXED) TRY(ensure_path<float>(b));
+  else TRY(ensure_path<double>(b));
+  PathState& P = precision == RVE_PREC_MIXED ? b->pf : b->pd;
+  const RveMeta& M = b->topo.meta[r];
+  RVE_CUDA_TRY(cudaDeviceSynchronize());  // no solve may be using the state
+  if (M.nf > 0) {
+    const int64_t n0 = b->topo.node_off_in[r];
+    std::vector<double> h(4 * size_t(M.nf), 0.0);
+    for (int a = 0; a < M.nf; ++a) {
+      const int i = b->topo.free_node_id[M.node_off + a];
+      const double* X = &b->topo.X_in[3 * (n0 + i)];
+      for (int k = 0; k < 3; ++k)
+        h[4 * a + k] = x[3 * i + k] - (F[3 * k] * X[0] + F[3 * k + 1] * X[1] + F[3 * k + 2] * X[2]);
+    }
+    RVE_CUDA_TRY(cudaMemcpy(static_cast<double*>(P.d_state) + 4 * size_t(M.node_off), h.data(),
+                            h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  const uint8_t one = 1;
+  RVE_CUDA_TRY(cudaMemcpy(P.d_valid + r, &one, 1, cudaMemcpyHostToDevice));
+  return RVE_OK;
+}
+
 void rve_batch_destroy(rve_batch* b) {
   if (!b) return;
   cudaSetDevice(b->device);

@@ -78,10 +78,20 @@ constexpr int min_blocks() {
 // FP32 rounding of the result); otherwise e^x - 1 with the hardware
 // exponential (__expf), where e^x - 1 is at least 0.39 |e^x| in magnitude so
 // no cancellation amplifies its error.  Both are evaluated and one selected.
+#ifndef RVE_EXPM1_ESTRIN
+#define RVE_EXPM1_ESTRIN 0
+#endif
 __device__ __forceinline__ float k_expm1(float x) {
+#if RVE_EXPM1_ESTRIN
+  const float x2 = x * x, x4 = x2 * x2;
+  const float a = fmaf(0.5f, x, 1.0f), b = fmaf(1.0f / 24.0f, x, 1.0f / 6.0f);
+  const float c = fmaf(1.0f / 720.0f, x, 1.0f / 120.0f), d = fmaf(1.0f / 40320.0f, x, 1.0f / 5040.0f);
+  const float p = x * fmaf(x4, fmaf(x2, d, c), fmaf(x2, b, a));
+#else
   const float p =
       x * (1.0f + x * (0.5f + x * (1.0f / 6.0f + x * (1.0f / 24.0f + x * (1.0f / 120.0f +
            x * (1.0f / 720.0f + x * (1.0f / 5040.0f + x * (1.0f / 40320.0f))))))));
+#endif
   const float q = __expf(x) - 1.0f;
   return fabsf(x) <= 0.5f ? p : q;
 }
