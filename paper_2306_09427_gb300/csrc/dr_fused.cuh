@@ -17,8 +17,8 @@
 //            a fixed CSR order, four entries per 8-byte load (runs padded
 //            with a zero slot); deterministic, no atomics (the paper's
 //            getInternalForces scatters with atomics, Sec. 4.3);
-//     check  every check_every iterations: ||f_free||_2 (products, per-thread,
-//            per-warp and cross-warp sums all in FP64)
+//     check  every check_every iterations: ||f_free||_2 (per-node terms in T,
+//            per-thread, per-warp and cross-warp sums in FP64)
 //            against max(tol R_aff, 1e-16 sum EA) and, with sigma_tol > 0,
 //            the estimated remaining stress error; damping re-estimated,
 //            c = s 2 sqrt(lambda) from the Rayleigh quotient lambda; thread 0
@@ -78,20 +78,10 @@ constexpr int min_blocks() {
 // FP32 rounding of the result); otherwise e^x - 1 with the hardware
 // exponential (__expf), where e^x - 1 is at least 0.39 |e^x| in magnitude so
 // no cancellation amplifies its error.  Both are evaluated and one selected.
-#ifndef RVE_EXPM1_ESTRIN
-#define RVE_EXPM1_ESTRIN 0
-#endif
 __device__ __forceinline__ float k_expm1(float x) {
-#if RVE_EXPM1_ESTRIN
-  const float x2 = x * x, x4 = x2 * x2;
-  const float a = fmaf(0.5f, x, 1.0f), b = fmaf(1.0f / 24.0f, x, 1.0f / 6.0f);
-  const float c = fmaf(1.0f / 720.0f, x, 1.0f / 120.0f), d = fmaf(1.0f / 40320.0f, x, 1.0f / 5040.0f);
-  const float p = x * fmaf(x4, fmaf(x2, d, c), fmaf(x2, b, a));
-#else
   const float p =
       x * (1.0f + x * (0.5f + x * (1.0f / 6.0f + x * (1.0f / 24.0f + x * (1.0f / 120.0f +
            x * (1.0f / 720.0f + x * (1.0f / 5040.0f + x * (1.0f / 40320.0f))))))));
-#endif
   const float q = __expf(x) - 1.0f;
   return fabsf(x) <= 0.5f ? p : q;
 }
@@ -778,17 +768,19 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
       }
       bool do_rebase = false;
       if (check) {
-        // ||f||^2, v.(f_new - f_old) and v.M v: every product and partial sum
-        // in FP64 (per thread, per warp, across warps); warp 0 finishes the
-        // cross-warp sum and its lane 0 takes every block-uniform decision
-        // once (convergence, damping) and publishes it in shared memory.
+        // ||f||^2, v.(f_new - f_old) and v.M v: each node's term in the loop
+        // type, every sum over nodes in FP64 (per thread, per warp, across
+        // warps); warp 0 finishes the cross-warp sum and its lane 0 takes every
+        // block-uniform decision once (convergence, damping) and publishes it
+        // in shared memory.  (GB300 runs FP64 at 1/64 of the FP32 rate: the
+        // per-node products in FP64 cost 8 % of the loop at checks every 50
+        // iterations.)
         double t3[3] = {0.0, 0.0, pm};
 #pragma unroll
         for (int q = 0; q < NPT; ++q) {
           if (tid + q * NT < nf) {
-            const double gx = double(fx[q]), gy = double(fy[q]), gz = double(fz[q]);
-            t3[0] += gx * gx + gy * gy + gz * gz;
-            t3[1] += double(vx[q]) * gx + double(vy[q]) * gy + double(vz[q]) * gz;
+            t3[0] += double(fx[q] * fx[q] + fy[q] * fy[q] + fz[q] * fz[q]);
+            t3[1] += double(vx[q] * fx[q] + vy[q] * fy[q] + vz[q] * fz[q]);
           }
         }
         t3[1] -= pre;
@@ -960,9 +952,8 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
           h4.w = T(0);
           H[a] = h4;
           if (pre_it) {
-            const double wx = double(nvx), wy = double(nvy), wz = double(nvz);
-            pre += wx * double(fx[q]) + wy * double(fy[q]) + wz * double(fz[q]);
-            pm += double(m) * (wx * wx + wy * wy + wz * wz);
+            pre += double(nvx * fx[q] + nvy * fy[q] + nvz * fz[q]);
+            pm += double(m * (nvx * nvx + nvy * nvy + nvz * nvz));
           }
           if (kinetic) ke_t += m * (nvx * nvx + nvy * nvy + nvz * nvz);
         }
