@@ -134,7 +134,24 @@ typedef struct rve_batch rve_batch; /* opaque, library owned */
  *               check exists to expose; the largest over the checks is kept.
  *               Read the records with rve_energy.  Batched precisions with
  *               viscous damping only (RVE_EINVAL otherwise); diagnostic, the
- *               iterates are those of the default kernel.  Default 0.
+ *               iterates are those of the two-phase kernel.  Default 0.
+ *  kernel       RVE_KERNEL_AUTO (0) or RVE_KERNEL_TWO_PHASE (1): the
+ *               two-phase kernel (a fiber phase, then a node-centric CSR
+ *               gather of the fiber forces; RVEs too large for one CTA's
+ *               shared memory stream their fiber data from L2/HBM): the
+ *               fastest on large batches.  RVE_KERNEL_NODE (2), for the
+ *               viscous damping modes: RVEs that fit one CTA run the
+ *               node-centric kernel (each thread owns free nodes and
+ *               evaluates their incident fibers itself: one barrier per DR
+ *               iteration, no fiber scratch; a fiber with two free ends is
+ *               evaluated at both ends, with exactly opposite forces); larger
+ *               RVEs of the mixed precision run on a thread-block cluster of
+ *               2-8 CTAs that holds the whole RVE in distributed shared
+ *               memory (lower latency per RVE, more SMs per RVE).  All
+ *               compute Algorithm 2's iterates (Sec. 3.2); the force sums at a
+ *               node are taken in other orders, so results differ at the
+ *               rounding level.  Default 0.
+ *  reserved_    must be 0.
  */
 typedef struct rve_options {
   double tol;
@@ -149,10 +166,15 @@ typedef struct rve_options {
   int32_t damping_mode;
   int32_t energy_check;
   double damping_scale;
+  int32_t kernel;
+  int32_t reserved_;
 } rve_options;
 
 #define RVE_DAMP_VISCOUS 0
 #define RVE_DAMP_KINETIC 1
+#define RVE_KERNEL_AUTO 0
+#define RVE_KERNEL_TWO_PHASE 1
+#define RVE_KERNEL_NODE 2
 
 /* Fill *opt with the defaults above.  Never fails. */
 void rve_options_default(rve_options* opt);
@@ -322,11 +344,18 @@ int rve_batch_get_info(const rve_batch* b, rve_batch_info* info);
 /*
  * Launch configuration of the batched path, per size bin.  Bins group RVEs
  * by footprint: resident bins (mode 0) hold a whole RVE in shared memory,
- * streamed bins (1, 2) read fiber data from L2/HBM.
+ * streamed bins (1, 2) read fiber data from L2/HBM, unless the mixed path
+ * holds them in a thread-block cluster:
+ *   kernel        which kernel runs the bin with the batch's options:
+ *                 0 two-phase, 1 node-centric (one CTA per RVE),
+ *                 2 node-centric over a cluster of `cluster` CTAs per RVE;
+ *   cluster       CTAs per RVE of kernel 2 (0 otherwise);
+ *   smem_bytes    dynamic shared memory per CTA of that kernel.
  */
 typedef struct rve_bin_info {
   int32_t n_rve, mode, threads, nodes_per_thread, ctas_per_sm, check_every;
   int64_t smem_bytes;
+  int32_t kernel, cluster;
 } rve_bin_info;
 /* Fill up to max entries for `precision` (RVE_PREC_MIXED or _BATCHED_F64);
  * returns the number of bins (0 before the first batched solve). */

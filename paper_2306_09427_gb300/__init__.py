@@ -5,7 +5,7 @@ marshalling only, every step of the solve runs in the CUDA kernels of
 ``librve.so``.  Importing this package fails loudly when the library has
 not been built: there is no CPU fallback.
 """
-from ._lib import (RVE_DAMP_KINETIC, RVE_DAMP_VISCOUS, RVE_EADMIT, RVE_ECUDA, RVE_EINVAL, RVE_ENOMEM, RVE_OK, RVE_PREC_BATCHED_F64,
+from ._lib import (RVE_DAMP_KINETIC, RVE_DAMP_VISCOUS, RVE_KERNEL_AUTO, RVE_KERNEL_NODE, RVE_KERNEL_TWO_PHASE, RVE_EADMIT, RVE_ECUDA, RVE_EINVAL, RVE_ENOMEM, RVE_OK, RVE_PREC_BATCHED_F64,
                    RVE_PREC_MIXED, RVE_PREC_PLAIN_F64, RVE_STATUS_CONVERGED, RVE_STATUS_EMPTY,
                    RVE_STATUS_MAX_ITER, RVE_STATUS_NONFINITE, RVE_STATUS_RUNNING, RveBatch, RveError, RveServer, lib, lib_path,
                    rve_batch_create, rve_batch_destroy, rve_batch_get_info, rve_batch_get_sizes,

@@ -17,13 +17,15 @@ RVE_STATUS_CONVERGED, RVE_STATUS_MAX_ITER, RVE_STATUS_NONFINITE, RVE_STATUS_EMPT
 RVE_STATUS_RUNNING = 4
 RVE_PREC_PLAIN_F64, RVE_PREC_MIXED, RVE_PREC_BATCHED_F64 = 0, 1, 2
 RVE_DAMP_VISCOUS, RVE_DAMP_KINETIC = 0, 1
+RVE_KERNEL_AUTO, RVE_KERNEL_TWO_PHASE, RVE_KERNEL_NODE = 0, 1, 2
 
 
 class rve_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("check_every", C.c_int32),
                 ("precision", C.c_int32), ("warm_start", C.c_int32), ("damping", C.c_double),
                 ("threads", C.c_int32), ("graphs", C.c_int32), ("sigma_tol", C.c_double),
-                ("damping_mode", C.c_int32), ("energy_check", C.c_int32), ("damping_scale", C.c_double)]
+                ("damping_mode", C.c_int32), ("energy_check", C.c_int32), ("damping_scale", C.c_double),
+                ("kernel", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class rve_batch_info(C.Structure):
@@ -66,7 +68,8 @@ rve_set_positions = _sig("rve_set_positions", C.c_int, [_P, _I64, _P, _I32, _P])
 
 class rve_bin_info(C.Structure):
     _fields_ = [("n_rve", C.c_int32), ("mode", C.c_int32), ("threads", C.c_int32), ("nodes_per_thread", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("check_every", C.c_int32), ("smem_bytes", C.c_int64)]
+                ("ctas_per_sm", C.c_int32), ("check_every", C.c_int32), ("smem_bytes", C.c_int64),
+                ("kernel", C.c_int32), ("cluster", C.c_int32)]
 
 
 rve_batch_get_bins = _sig("rve_batch_get_bins", C.c_int, [_P, _I32, _I32, C.POINTER(rve_bin_info)])

@@ -25,6 +25,10 @@ struct Bin {
   int per_sm = 1; // CTAs per SM the footprint allows (bin key)
   int check_every = 0;  // 0: the batch option; > 0: set by the autotuner
   size_t smem = 0;
+  size_t smem_node = 0;  // > 0: the node-centric kernel can run this bin with this much shared memory
+  int cl = 0;            // > 0: the cluster kernel runs this bin, cl CTAs per RVE ...
+  int cl_npt = 1;        // ... with cl_npt free nodes per thread ...
+  size_t smem_cluster = 0;  // ... and this much shared memory per CTA
   std::vector<Work> work;
   Work* d_work = nullptr;    // canonical order
   Work* d_sorted = nullptr;  // longest-first order written before each launch (bins up to LPT_MAX)
@@ -36,8 +40,11 @@ constexpr int LPT_MAX = 16384;  // bins up to this size are sorted on the device
 struct BinKey {
   int mode, nt, npt, per_sm;
   size_t smem;
+  int cl = 0, cl_npt = 1;  // cluster configuration (streamed RVEs, mixed precision): part of the key, so an
+                           // RVE's cluster split does not depend on the other RVEs of its batch
+  size_t smem_cl = 0;
   bool operator==(const BinKey& o) const {
-    return mode == o.mode && nt == o.nt && npt == o.npt && per_sm == o.per_sm;
+    return mode == o.mode && nt == o.nt && npt == o.npt && per_sm == o.per_sm && cl == o.cl && cl_npt == o.cl_npt;
   }
 };
 
@@ -124,6 +131,7 @@ struct rve_batch {
   uint32_t* d_fij = nullptr;
   rvegpu::FibD* d_fb = nullptr;
   uint16_t* d_csr = nullptr;
+  uint16_t* d_nord = nullptr;
   uint32_t* d_ncsr = nullptr;
   float* d_ncap = nullptr;
   rvegpu::PathState pf, pd;

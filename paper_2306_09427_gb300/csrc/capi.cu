@@ -34,6 +34,7 @@ int launch_bin(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
   if (a.kinetic) return launch_bin_kinetic(a, bin, s);
   return a.energy ? launch_bin_energy(a, bin, s) : launch_bin_viscous(a, bin, s);
 }
+int cluster_capacity_f32(int npt, int cl, size_t smem, int* n_clusters);
 int plain_scratch_bytes(int nf_max, int na_max);
 int plain_solve_one(rve_batch* b, int r, int out, const double* F, double tol, int max_iter, double* sigma,
                     int32_t* iters, int32_t* status, cudaStream_t s);
@@ -86,6 +87,9 @@ int valid_options(const rve_options& o) {
   if (o.energy_check != 0 && o.energy_check != 1) return fail(RVE_EINVAL, "energy_check must be 0 or 1");
   if (o.energy_check && (o.precision == RVE_PREC_PLAIN_F64 || o.damping_mode == RVE_DAMP_KINETIC))
     return fail(RVE_EINVAL, "the energy balance runs on the batched precisions with viscous damping");
+  if (o.reserved_ != 0) return fail(RVE_EINVAL, "reserved_ must be 0");
+  if (o.kernel != RVE_KERNEL_AUTO && o.kernel != RVE_KERNEL_TWO_PHASE && o.kernel != RVE_KERNEL_NODE)
+    return fail(RVE_EINVAL, "kernel must be RVE_KERNEL_AUTO, RVE_KERNEL_TWO_PHASE or RVE_KERNEL_NODE");
   if (o.threads != 0 && o.threads != 64 && o.threads != 128 && o.threads != 256 && o.threads != 512 &&
       o.threads != 1024)
     return fail(RVE_EINVAL, "threads must be 0, 64, 128, 256, 512 or 1024");
@@ -129,6 +133,82 @@ int choose_key(int nf, int na, int csr_len, int threads, BinKey& k) {
   const int by_smem = int((228 * 1024) / (sm + 1024 + 512));
   const int by_thr = 2048 / nt;
   k = BinKey{mode, nt, npt, std::max(1, std::min(by_smem, by_thr)), sm};
+  return RVE_OK;
+}
+
+// Incidence slots of the busiest thread of RVE r in the node-centric layout
+// (nt threads, npt free nodes each, dealt by node_rank over the
+// decreasing-degree order).
+int node_slots(const rve_batch* b, int64_t r, int nt, int npt) {
+  const RveMeta& M = b->topo.meta[size_t(r)];
+  const uint16_t* csr = b->topo.csr.data() + M.csr_off;
+  auto deg = [&](int a) {
+    const uint32_t w = b->topo.ncsr[size_t(M.node_off + a)];
+    int d = 0;
+    for (uint32_t k = 0; k < (w & 0xffu); ++k) d += (uint32_t(csr[(w >> 8) + k]) >> 1) < uint32_t(M.na) ? 1 : 0;
+    return d;
+  };
+  int best = 0;
+  for (int t = 0; t < nt; ++t) {
+    int sl = 0;
+    for (int q = 0; q < npt; ++q) {
+      const int k = node_rank(q, t, nt);
+      if (k < M.nf) sl += deg(int(b->topo.nord[size_t(M.node_off + k)]));
+    }
+    best = std::max(best, sl);
+  }
+  return best;
+}
+
+// Shared memory the node-centric kernel needs for every RVE of a work list
+// at (nt, npt); 0 when one of them does not fit or holds more free nodes
+// than the threads own.
+template <typename T>
+size_t node_smem(const rve_batch* b, const std::vector<Work>& work, int nt, int npt) {
+  size_t need = 0;
+  for (const Work& w : work) {
+    const RveMeta& M = b->topo.meta[size_t(w.rve)];
+    if (M.nf > nt * npt) return 0;
+    need = std::max(need, smem_node<T>(M.nf, node_slots(b, w.rve, nt, npt), nt));
+  }
+  return need <= SMEM_LIMIT - 1024 ? need : 0;
+}
+
+// Free nodes per thread preferred by the cluster kernel when both fit: 2
+// (half the SMs per RVE of 1; each thread walks twice the slots).
+#ifndef RVE_CLUSTER_NPT_PREF
+#define RVE_CLUSTER_NPT_PREF 2
+#endif
+
+// Cluster configuration of a streamed RVE (mixed precision), from the RVE
+// alone: the fewest CTAs of CLUSTER_NT threads that own every free node,
+// with RVE_CLUSTER_NPT_PREF nodes per thread if that fits one CTA's shared
+// memory, else the other choice; cl = 0 when neither fits.
+void cluster_key(const rve_batch* b, int64_t r, BinKey& k) {
+  k.cl = 0;
+  k.cl_npt = 1;
+  k.smem_cl = 0;
+  const int nf = b->topo.meta[size_t(r)].nf;
+  const int order[2] = {RVE_CLUSTER_NPT_PREF, 3 - RVE_CLUSTER_NPT_PREF};
+  for (int npt : order) {
+    const int cl = std::max(2, (nf + npt * CLUSTER_NT - 1) / (npt * CLUSTER_NT));
+    if (cl > CLUSTER_MAX) continue;
+    const size_t need = smem_cluster<float>(nf, node_slots(b, r, cl * CLUSTER_NT, npt), CLUSTER_NT);
+    if (need > SMEM_LIMIT - 1024) continue;
+    k.cl = cl;
+    k.cl_npt = npt;
+    k.smem_cl = need;
+    return;
+  }
+}
+
+// The device must hold at least one cluster of a bin's configuration;
+// otherwise the bin runs the streamed two-phase kernel.
+int check_cluster(Bin& bin) {
+  if (bin.cl == 0) return RVE_OK;
+  int n_clusters = 0;
+  TRY(cluster_capacity_f32(bin.cl_npt, bin.cl, bin.smem_cluster, &n_clusters));
+  if (n_clusters <= 0) bin.cl = 0;
   return RVE_OK;
 }
 
@@ -227,6 +307,7 @@ int ensure_path(rve_batch* b) {
     const RveMeta& M = b->topo.meta[r];
     BinKey k;
     TRY(choose_key<T>(M.nf, M.na, M.csr_len, b->opt.threads, k));
+    if (k.mode != 0 && std::is_same<T, float>::value) cluster_key(b, r, k);
     P.key_of[r] = k;
     size_t j = 0;
     while (j < keys.size() && !(keys[j] == k)) ++j;
@@ -235,6 +316,7 @@ int ensure_path(rve_batch* b) {
       members.emplace_back();
     }
     keys[j].smem = std::max(keys[j].smem, k.smem);
+    keys[j].smem_cl = std::max(keys[j].smem_cl, k.smem_cl);
     members[j].push_back(int(r));
   }
   // streamed-bin scratch offsets (main solves and tangent directions)
@@ -264,6 +346,18 @@ int ensure_path(rve_batch* b) {
     Bin tb = bin;
     Bin mb = bin;
     for (int r : mem) bin.work.push_back(Work{r, r, b->topo.meta[r].node_off, 0, scr_of[r], 0});
+    if (bin.mode == 0) {
+      bin.smem_node = node_smem<T>(b, bin.work, bin.nt, bin.npt);
+    } else {
+      bin.cl = keys[j].cl;
+      bin.cl_npt = keys[j].cl_npt;
+      bin.smem_cluster = keys[j].smem_cl;
+      TRY(check_cluster(bin));
+    }
+    tb.smem_node = mb.smem_node = bin.smem_node;
+    tb.cl = mb.cl = bin.cl;
+    tb.cl_npt = mb.cl_npt = bin.cl_npt;
+    tb.smem_cluster = mb.smem_cluster = bin.smem_cluster;
     for (int r : mem)
       for (int d = 0; d < N_DIRS; ++d) {
         const Work w{r, int32_t(d * n + r), int32_t(d * b->total_nf + b->topo.meta[r].node_off), 1,
@@ -369,6 +463,8 @@ DrArgs<T> make_args(rve_batch* b, const double* F, double tol, int max_iter, dou
   a.fb = b->d_fb;
   a.csr = b->d_csr;
   a.ncsr = b->d_ncsr;
+  a.nord = b->d_nord;
+  a.node_kernel = b->opt.kernel == RVE_KERNEL_NODE ? 1 : 0;
   a.ncap = b->d_ncap;
   a.work = nullptr;
   a.n_work = 0;
@@ -720,6 +816,7 @@ int autotune_path(rve_batch* b, const double* F, int reps, cudaStream_t s, doubl
         cand.npt = k.npt;
         cand.per_sm = k.per_sm;
         cand.smem = std::max(k.smem, size_t(0));
+        cand.smem_node = cand.mode == 0 ? node_smem<T>(b, bin.work, k.nt, k.npt) : 0;
         cand.check_every = kc;
         float t = 0.f;
         TRY(run_one(b, cand, a, s));
@@ -734,6 +831,7 @@ int autotune_path(rve_batch* b, const double* F, int reps, cudaStream_t s, doubl
     bin.npt = best.npt;
     bin.per_sm = best.per_sm;
     bin.smem = best.smem;
+    bin.smem_node = best.smem_node;
     bin.check_every = best.check_every;
     after += t_best;
   }
@@ -744,6 +842,10 @@ int autotune_path(rve_batch* b, const double* F, int reps, cudaStream_t s, doubl
       (*tb)[j].npt = P.bins[j].npt;
       (*tb)[j].per_sm = P.bins[j].per_sm;
       (*tb)[j].smem = P.bins[j].smem;
+      (*tb)[j].smem_node = P.bins[j].smem_node;
+      (*tb)[j].cl = P.bins[j].cl;
+      (*tb)[j].cl_npt = P.bins[j].cl_npt;
+      (*tb)[j].smem_cluster = P.bins[j].smem_cluster;
       (*tb)[j].check_every = P.bins[j].check_every;
     }
   cudaEventDestroy(e0);
@@ -777,6 +879,7 @@ void rve_options_default(rve_options* o) {
   o->threads = 0;
   o->damping_mode = RVE_DAMP_VISCOUS;
   o->damping_scale = DAMP_SCALE;
+  o->kernel = RVE_KERNEL_AUTO;
 }
 
 const char* rve_last_error(void) { return g_error.c_str(); }
@@ -838,6 +941,7 @@ int rve_batch_create(rve_batch** out, int device, int64_t n_rve, const int64_t* 
   if ((rc = upload(b, &b->d_fb, b->topo.fb)) != RVE_OK) return bail(rc);
   if ((rc = upload(b, &b->d_csr, b->topo.csr)) != RVE_OK) return bail(rc);
   if ((rc = upload(b, &b->d_ncsr, b->topo.ncsr)) != RVE_OK) return bail(rc);
+  if ((rc = upload(b, &b->d_nord, b->topo.nord)) != RVE_OK) return bail(rc);
   if ((rc = upload(b, &b->d_ncap, b->topo.ncap)) != RVE_OK) return bail(rc);
   int nf_max = 0, na_max = 0;
   for (const RveMeta& M : b->topo.meta) {
@@ -968,6 +1072,10 @@ int solve_items(rve_batch* b, const int64_t* ids, const int32_t* outs, int64_t m
     bins[j].npt = P.bins[j].npt;
     bins[j].per_sm = P.bins[j].per_sm;
     bins[j].smem = P.bins[j].smem;
+    bins[j].smem_node = P.bins[j].smem_node;
+    bins[j].cl = P.bins[j].cl;
+    bins[j].cl_npt = P.bins[j].cl_npt;
+    bins[j].smem_cluster = P.bins[j].smem_cluster;
   }
   for (int64_t k = 0; k < m; ++k) {
     const int r = int(ids[k]);
@@ -1222,7 +1330,21 @@ int rve_batch_get_bins(const rve_batch* b, int32_t precision, int32_t max, rve_b
       out[n].nodes_per_thread = x.npt;
       out[n].ctas_per_sm = x.per_sm;
       out[n].check_every = x.check_every > 0 ? x.check_every : b->opt.check_every;
+      const bool alt = b->opt.kernel == RVE_KERNEL_NODE && !b->opt.energy_check &&
+                       b->opt.damping_mode == RVE_DAMP_VISCOUS;
+      out[n].kernel = 0;
+      out[n].cluster = 0;
       out[n].smem_bytes = int64_t(x.smem);
+      if (alt && x.mode == 0 && x.smem_node > 0) {
+        out[n].kernel = 1;
+        out[n].smem_bytes = int64_t(x.smem_node);
+      } else if (alt && x.mode != 0 && x.cl > 0) {
+        out[n].kernel = 2;
+        out[n].cluster = x.cl;
+        out[n].threads = CLUSTER_NT;
+        out[n].nodes_per_thread = x.cl_npt;
+        out[n].smem_bytes = int64_t(x.smem_cluster);
+      }
     }
     ++n;
   }

@@ -134,6 +134,31 @@ inline size_t smem_streamed(int nf, int na, int nt, bool scr_in_smem) {
          red_bytes(nt);
 }
 
+// Node-centric layout (dr_node_kernel): two H buffers (nf+1 4-vectors each),
+// the reduction buffer, then per incidence slot two 4-vectors (chord/strain
+// and law parameters), `slots` slots per thread (the busiest thread's
+// count) for nt threads.
+template <typename T>
+inline size_t smem_node(int nf, int slots, int nt) {
+  const size_t v4 = 4 * sizeof(T);
+  return 2 * align_up(size_t(nf + 1) * v4, 16) + red_bytes(nt) + size_t(slots) * 2 * size_t(nt) * v4;
+}
+// Cluster layout (dr_cluster_kernel), per CTA: two replicas of the H
+// buffers (nf+1 4-vectors each), the reduction buffer, CTA 0's gather rows
+// (8 x 12 doubles), then the incidence slots of the CTA's threads.
+constexpr int CLUSTER_NT = 512;  // threads per CTA of the cluster kernel
+constexpr int CLUSTER_MAX = 8;   // CTAs per cluster (the portable limit)
+template <typename T>
+inline size_t smem_cluster(int nf, int slots, int nt) {
+  const size_t v4 = 4 * sizeof(T);
+  return 2 * align_up(size_t(nf + 1) * v4, 16) + red_bytes(nt) + align_up(8 * 12 * sizeof(double), 16) +
+         size_t(slots) * 2 * size_t(nt) * v4;
+}
+// Free node dealt to thread t as its q-th node: position in the
+// decreasing-degree order, snaking (q even: q nt + t; q odd: (q+1) nt - 1 - t)
+// so that each thread's total is balanced.
+__host__ __device__ inline int node_rank(int q, int t, int nt) { return (q & 1) ? (q + 1) * nt - 1 - t : q * nt + t; }
+
 constexpr int NODES_PER_THREAD = 4;  // free nodes owned per thread (registers)
 constexpr int MAX_THREADS = 1024;
 constexpr size_t SMEM_LIMIT = 232448;  // 227 KB opt-in per CTA
@@ -149,6 +174,8 @@ struct DrArgs {
                            // entries with (na << 1) (the zero scratch slot)
   const uint32_t* ncsr;    // per free node: (local CSR begin << 8) | count
   const float* ncap;       // per free node: STEP_CAP * min incident L0
+  const uint16_t* nord;    // per RVE (node offsets): free nodes by decreasing degree
+  int32_t node_kernel;     // 1: resident bins run dr_node_kernel, streamed bins with a cluster layout dr_cluster_kernel
   const Work* work;
   int32_t n_work;
   const double* F;         // 9 per output index
@@ -202,6 +229,7 @@ struct HostTopology {
   std::vector<uint16_t> csr;
   std::vector<uint32_t> ncsr;
   std::vector<float> ncap;
+  std::vector<uint16_t> nord;         // per RVE: free nodes by decreasing degree
   std::vector<int32_t> free_node_id;  // original RVE-local id of each free node
   std::vector<int64_t> node_off_in;   // input node offsets (position export)
   std::vector<double> X_in;           // input coordinates (position export)

@@ -168,6 +168,17 @@ void order_rve(HostTopology& T, int64_t r) {
     const uint32_t w = T.ncsr[size_t(M.node_off + a)];
     std::copy(runs[size_t(a)].begin(), runs[size_t(a)].end(), csr + (w >> 8));
   }
+  // free nodes by decreasing degree (ties by index): the node-centric kernel
+  // deals them to threads in this order, so the nodes a warp owns at one
+  // time have (nearly) the same number of fibers
+  std::vector<std::pair<int, int32_t>> by_deg(static_cast<size_t>(M.nf));
+  for (int32_t a = 0; a < M.nf; ++a) {
+    int real = 0;
+    for (uint16_t x : runs[size_t(a)]) real += (uint32_t(x) >> 1) != na ? 1 : 0;
+    by_deg[size_t(a)] = {-real, a};
+  }
+  std::sort(by_deg.begin(), by_deg.end());
+  for (int32_t k = 0; k < M.nf; ++k) T.nord[size_t(M.node_off + k)] = uint16_t(by_deg[size_t(k)].second);
 }
 
 }  // namespace
@@ -366,6 +377,7 @@ int build_topology(int64_t n_rve, const int64_t* node_off, const double* X, cons
   // bank-aware orders; every RVE owns disjoint segments, so RVEs run on
   // separate host threads
   const int64_t n_thr = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), n_rve / 16));
+  T.nord.assign(T.ncsr.size(), 0);
   std::vector<std::thread> pool;
   for (int64_t t = 0; t < n_thr; ++t)
     pool.emplace_back([&T, t, n_thr, n_rve] {

@@ -6,6 +6,9 @@
     python -m paper_2306_09427_gb300.measure orientation  # orientation tensors of 1024 x 10^3 RVEs (HBM-bound)
     python -m paper_2306_09427_gb300.measure streamed  # 152 RVEs of side 15-16 (streamed kernel variants)
 
+Option --kernel node runs the node-centric kernels (clusters for RVEs too
+large for one CTA) instead of the two-phase kernel.
+
 Each line gives the batched mixed-precision path (one solve of the whole
 batch, CUDA events on a created stream, warm-up excluded, median of the
 timed repeats) and the plain FP64 per-RVE path on a subset of the same RVEs
@@ -23,7 +26,8 @@ import numpy as np
 
 import rvegen
 
-from ._lib import RVE_PREC_BATCHED_F64, RVE_PREC_MIXED, RVE_PREC_PLAIN_F64, RveBatch
+from ._lib import (RVE_KERNEL_AUTO, RVE_KERNEL_NODE, RVE_KERNEL_TWO_PHASE, RVE_PREC_BATCHED_F64, RVE_PREC_MIXED,
+                   RVE_PREC_PLAIN_F64, RveBatch)
 
 
 def _time_solves(b, Fd, reps, stream, tangent=False):
@@ -85,8 +89,11 @@ def _orientation(b, Fd, stream, reps, res):
     return res
 
 
+KERNELS = {"auto": RVE_KERNEL_AUTO, "two-phase": RVE_KERNEL_TWO_PHASE, "node": RVE_KERNEL_NODE}
+
+
 def run(config: str, reps: int = 5, plain_subset: int = 32, tol: float = 3e-7, autotune: bool = True,
-        device: int = 0, damping_scale: float = 1.0) -> dict:
+        device: int = 0, damping_scale: float = 1.0, kernel: str = "auto") -> dict:
     import torch
     torch.cuda.set_device(device)
     stream = torch.cuda.Stream()
@@ -114,11 +121,11 @@ def run(config: str, reps: int = 5, plain_subset: int = 32, tol: float = 3e-7, a
     n = len(nets)
     prec = RVE_PREC_BATCHED_F64 if config == "single" else RVE_PREC_MIXED
     b = RveBatch(pk, device=device, precision=prec, tol=tol_m, graphs=1, warm_start=int(config == "tangent"),
-                 damping_scale=damping_scale)
+                 damping_scale=damping_scale, kernel=KERNELS[kernel])
     t_create = time.perf_counter() - t0
     Fd = torch.tensor(Fs.reshape(-1, 9), dtype=torch.float64, device=f"cuda:{device}")
     res = {"config": config, "n_rve": n, "create_s": t_create, "precision": "f64 batched" if config == "single"
-           else "mixed", "tol_rel_residual": tol_m, "damping_scale": damping_scale}
+           else "mixed", "tol_rel_residual": tol_m, "damping_scale": damping_scale, "kernel": kernel}
     if config == "orientation":
         return _orientation(b, Fd, stream, reps, res)
     if config == "tangent":
@@ -162,9 +169,11 @@ def main():
     ap.add_argument("--plain-subset", type=int, default=32)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--damping-scale", type=float, default=1.0, help="s in c = s * 2 sqrt(lambda), both paths")
+    ap.add_argument("--kernel", choices=sorted(KERNELS), default="auto",
+                    help="batched kernel: two-phase (auto) or node-centric with clusters for large RVEs (node)")
     a = ap.parse_args()
     print(json.dumps(run(a.config, a.reps, a.plain_subset, autotune=not a.no_autotune,
-                         damping_scale=a.damping_scale)))
+                         damping_scale=a.damping_scale, kernel=a.kernel)))
 
 
 if __name__ == "__main__":
