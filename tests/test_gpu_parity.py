@@ -156,7 +156,7 @@ def test_kinetic_damping_converges_to_same_state(rve, small_case, precision, tol
 
 # --------------------------------------- full-size uniform batch (1024 x 10^3)
 
-BENCH_OPTS = dict(damping_scale=0.7)  # bench.py's options beyond the library defaults
+BENCH_OPTS = dict(damping_scale=0.7, tol=1e-6, sigma_tol=2e-5)  # bench.py's options beyond the library defaults
 
 
 @pytest.mark.parametrize("opts", [{}, BENCH_OPTS], ids=["defaults", "bench"])
@@ -178,7 +178,7 @@ def test_uniform_full_batch_sampled(rve, opts):
     assert np.isfinite(s).all()
     assert np.abs(s - s.transpose(0, 2, 1)).max() <= 1e-12 * np.abs(s).max()
     # every RVE against a tight FP64 solve of the same DR (same start, same rule)
-    b64 = rve.RveBatch(rvegen.pack(nets), precision=rve.RVE_PREC_BATCHED_F64, tol=1e-10, sigma_tol=0.0, **opts)
+    b64 = rve.RveBatch(rvegen.pack(nets), precision=rve.RVE_PREC_BATCHED_F64, **dict(opts, tol=1e-10, sigma_tol=0.0))
     s64, _, _ = b64.solve(_F(Fs))
     s64 = s64.cpu().numpy().reshape(-1, 3, 3)
     e = np.linalg.norm((s - s64).reshape(1024, -1), axis=1) / np.linalg.norm(s64.reshape(1024, -1), axis=1)
