@@ -26,6 +26,7 @@ struct Bin {
   int check_every = 0;  // 0: the batch option; > 0: set by the autotuner
   size_t smem = 0;
   size_t smem_node = 0;  // > 0: the node-centric kernel can run this bin with this much shared memory
+  bool pdl = false;      // launched as a programmatic dependent of the launch before it on its stream
   int cl = 0;            // > 0: the cluster kernel runs this bin, cl CTAs per RVE ...
   int cl_npt = 1;        // ... with cl_npt free nodes per thread ...
   size_t smem_cluster = 0;  // ... and this much shared memory per CTA
@@ -139,6 +140,7 @@ struct rve_batch {
   double* d_pl = nullptr;
   size_t pl_bytes = 0;
   double* h_pl = nullptr;  // pinned, reduction read-back
+  int32_t* d_pdl_done = nullptr;  // CTAs finished of the dependent part of a split launch
   // streams for concurrent bins
   cudaStream_t side[rvegpu::N_SIDE_STREAMS] = {};
   cudaStream_t hstream = nullptr;  // host-buffer solves

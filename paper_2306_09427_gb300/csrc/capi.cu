@@ -408,11 +408,44 @@ int ensure_path(rve_batch* b) {
 // Run a list of bins on `s`, concurrently on side streams when there are several.
 constexpr size_t KERNEL_TIMING_MAX = 65536;  // launches recorded per rve_set_kernel_timing
 
+// The costliest RVEs of a large resident bin (the head of the longest-first
+// list) run in a launch of their own whose shared-memory request leaves no
+// room for another CTA on their SM: an RVE alone on an SM takes ~25 % less
+// time per DR iteration than two sharing one, and these RVEs set the end of
+// the solve.  The rest of the bin follows on the same stream as a
+// programmatic dependent launch, which starts as soon as every CTA of the
+// first has begun (so those are resident first) and runs beside it on the
+// other SMs.  Same kernel and arithmetic, so the results do not change.
+constexpr int EXCL_MAX = 8;                // RVEs given SMs of their own, per bin
+constexpr size_t EXCL_SMEM = 224 * 1024;   // dynamic shared memory of their CTAs
+int excl_count(const Bin& use) {
+  if (use.mode != 0 || use.per_sm < 2 || use.n < 64) return 0;
+  return std::min(EXCL_MAX, use.n / 64);
+}
+
 template <typename T>
-int run_one(rve_batch* b, const Bin& bin, const DrArgs<T>& a, cudaStream_t s) {
+int launch_split(rve_batch* b, const Bin& use, const DrArgs<T>& a, cudaStream_t s) {
+  const int k = excl_count(use);
+  if (k == 0) return launch_bin(a, use, s);
+  Bin heavy = use, light = use;
+  heavy.n = k;
+  heavy.smem = std::max(use.smem, EXCL_SMEM);
+  if (use.smem_node > 0) heavy.smem_node = std::max(use.smem_node, EXCL_SMEM);
+  light.d_work = use.d_work + k;
+  light.n = use.n - k;
+  light.pdl = true;
+  DrArgs<T> al = a;
+  al.pdl_done = b->d_pdl_done;
+  TRY(launch_bin(a, heavy, s));
+  return launch_bin(al, light, s);
+}
+
+template <typename T>
+int run_one(rve_batch* b, const Bin& bin, const DrArgs<T>& a, cudaStream_t s, bool split = false) {
   Bin use;
   TRY(launch_sorted(b, bin, s, a.last_iters, use));
-  if (!b->timing || b->n_kev >= KERNEL_TIMING_MAX) return launch_bin(a, use, s);
+  auto launch = [&]() { return split ? launch_split(b, use, a, s) : launch_bin(a, use, s); };
+  if (!b->timing || b->n_kev >= KERNEL_TIMING_MAX) return launch();
   // events on the launching stream bracket the fused kernel alone
   if (2 * b->n_kev + 2 > b->kev.size()) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -426,19 +459,24 @@ int run_one(rve_batch* b, const Bin& bin, const DrArgs<T>& a, cudaStream_t s) {
   }
   const size_t k = 2 * b->n_kev++;
   RVE_CUDA_TRY(cudaEventRecord(b->kev[k], s));
-  TRY(launch_bin(a, use, s));
+  TRY(launch());
   RVE_CUDA_TRY(cudaEventRecord(b->kev[k + 1], s));
   return RVE_OK;
 }
 
 template <typename T>
-int run_bins(rve_batch* b, const std::vector<Bin>& bins, const DrArgs<T>& a, cudaStream_t s, bool fork = true) {
+// split: a lone bin may give its costliest RVEs SMs of their own (whole-
+// batch solves; subset solves, whose concurrent calls would queue on the
+// one high-priority stream, keep one launch per bin)
+int run_bins(rve_batch* b, const std::vector<Bin>& bins, const DrArgs<T>& a, cudaStream_t s, bool fork = true,
+             bool split = false) {
   std::vector<const Bin*> live;
   for (const Bin& x : bins)
     if (x.n > 0) live.push_back(&x);
   if (live.empty()) return RVE_OK;
   if (live.size() == 1 || !fork) {
-    for (const Bin* x : live) TRY(run_one(b, *x, a, s));
+    // one bin (or one stream): its costliest RVEs may take SMs of their own
+    for (const Bin* x : live) TRY(run_one(b, *x, a, s, split && live.size() == 1));
     return RVE_OK;
   }
   RVE_CUDA_TRY(cudaEventRecord(b->ev_fork, s));
@@ -490,6 +528,7 @@ DrArgs<T> make_args(rve_batch* b, const double* F, double tol, int max_iter, dou
   a.resume = nullptr;
   a.vel = nullptr;
   a.energy = nullptr;
+  a.pdl_done = nullptr;
   return a;
 }
 
@@ -527,13 +566,13 @@ int solve_all(rve_batch* b, const double* F, double tol, int max_iter, double* s
     TRY(ensure_path<float>(b));
     DrArgs<float> a = make_args<float>(b, F, tol, max_iter, sigma, iters, status, b->pf.d_state, b->opt.warm_start);
     if (b->opt.energy_check) TRY(energy_buffer(b, b->pf, &a.energy));
-    return run_bins(b, b->pf.bins, a, s);
+    return run_bins(b, b->pf.bins, a, s, true, true);
   }
   if (prec == RVE_PREC_BATCHED_F64) {
     TRY(ensure_path<double>(b));
     DrArgs<double> a = make_args<double>(b, F, tol, max_iter, sigma, iters, status, b->pd.d_state, b->opt.warm_start);
     if (b->opt.energy_check) TRY(energy_buffer(b, b->pd, &a.energy));
-    return run_bins(b, b->pd.bins, a, s);
+    return run_bins(b, b->pd.bins, a, s, true, true);
   }
   TRY(ensure_path<double>(b));  // state buffer shared with the FP64 batched path
   for (int64_t r = 0; r < b->n_rve; ++r)
@@ -717,7 +756,7 @@ int mandel_batched(rve_batch* b, const double* F, double h, double tol, int max_
   a1.iters = b->d_tanI;
   a1.status = b->d_tanSt;
   a1.state = static_cast<double*>(P.d_tan_state);
-  TRY(run_bins(b, P.man_bins, a1, s));
+  TRY(run_bins(b, P.man_bins, a1, s, true, true));
   if (n > 0) {
     mandel_finish<<<int((n + 127) / 128 < 4096 ? (n + 127) / 128 : 4096), 128, 0, s>>>(
         F, sigma, b->d_tanS, b->d_tanSt, n, h, C, status);
@@ -754,7 +793,7 @@ int tangent_batched(rve_batch* b, const double* F, double h, double tol, int max
   a1.iters = b->d_tanI;
   a1.status = b->d_tanSt;
   a1.state = static_cast<double*>(P.d_tan_state);
-  TRY(run_bins(b, P.tan_bins, a1, s));
+  TRY(run_bins(b, P.tan_bins, a1, s, true, true));
   if (n > 0) {
     tan_finish<<<512, 256, 0, s>>>(b->d_tanS, b->d_tanSt, n, h, dsdF, status);
     RVE_CUDA_TRY(cudaGetLastError());
@@ -950,6 +989,8 @@ int rve_batch_create(rve_batch** out, int device, int64_t n_rve, const int64_t* 
   }
   b->pl_bytes = size_t(plain_scratch_bytes(nf_max, na_max)) + 16 * 256;
   if ((rc = dalloc(b, reinterpret_cast<void**>(&b->d_pl), b->pl_bytes)) != RVE_OK) return bail(rc);
+  if ((rc = dalloc(b, reinterpret_cast<void**>(&b->d_pdl_done), sizeof(int32_t))) != RVE_OK) return bail(rc);
+  if (cudaMemset(b->d_pdl_done, 0, sizeof(int32_t)) != cudaSuccess) return bail(fail(RVE_ECUDA, "cudaMemset failed"));
   if (cudaMallocHost(reinterpret_cast<void**>(&b->h_pl), 64 * sizeof(double)) != cudaSuccess)
     return bail(fail(RVE_ENOMEM, "cudaMallocHost failed"));
   for (int k = 0; k < N_SIDE_STREAMS; ++k) {

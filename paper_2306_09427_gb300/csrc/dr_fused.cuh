@@ -476,6 +476,27 @@ __device__ __forceinline__ void rebase(const DrArgs<T>& A, const Work& wk, const
   __syncthreads();
 }
 
+// End of a CTA of a programmatic dependent launch (A.pdl_done set): the last
+// CTA to finish waits until the launch it depends on has completed and its
+// writes are visible, so that this launch's completion implies that one's
+// for whatever follows on the stream.  It then resets the counter for the
+// next launch (graph replays included).
+template <typename T>
+__device__ __forceinline__ void pdl_epilogue(const DrArgs<T>& A) {
+  if (A.pdl_done == nullptr) return;
+  __shared__ int sLast;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    sLast = atomicAdd(A.pdl_done, 1) == A.n_work - 1;
+  }
+  __syncthreads();
+  if (sLast) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (threadIdx.x == 0) *A.pdl_done = 0;
+  }
+}
+
 // VAR selects the loop variant, each its own instantiation so that the
 // viscous default carries none of the others' code or registers:
 // VAR_VISCOUS (adaptive or fixed viscous damping), VAR_KINETIC (kinetic
@@ -502,6 +523,10 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
   // relative balance error seen
   __shared__ double sEn[8];
 
+  // a launch that follows this one as a programmatic dependent (the rest of a
+  // bin whose costliest RVEs run here, one per SM) may start once every CTA
+  // of this launch is resident; it reads nothing written here
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const Work wk = A.work[blockIdx.x];
   const RveMeta M = A.meta[wk.rve];
   const int tid = threadIdx.x;
@@ -1003,6 +1028,7 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
       if (A.iters) A.iters[wk.out] = it;
       if (A.status) A.status[wk.out] = status;
     }
+    pdl_epilogue(A);
     return;
   }
 
@@ -1061,6 +1087,7 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_fused_kernel(const Dr
     if (A.iters) A.iters[wk.out] = it;
     if (A.status) A.status[wk.out] = st;
   }
+  pdl_epilogue(A);
 }
 
 }  // namespace rvegpu

@@ -26,6 +26,32 @@ int set_smem(K fn, size_t smem, int (&smem_set)[64], std::mutex& mu) {
   return RVE_OK;
 }
 
+// Launch fn<<<grid, block, smem, s>>>(arg); with pdl, as a programmatic
+// dependent of the launch before it on s: it may start once every CTA of
+// that launch has signalled (griddepcontrol.launch_dependents, at the top of
+// the DR kernels) instead of when that launch ends.  It reads nothing that
+// launch writes.  Graph capture keeps the edge.
+template <typename K, typename Arg>
+int launch_k(K fn, unsigned grid, unsigned block, size_t smem, cudaStream_t s, bool pdl, const Arg& arg) {
+  if (!pdl) {
+    fn<<<grid, block, smem, s>>>(arg);
+    RVE_CUDA_TRY(cudaGetLastError());
+    return RVE_OK;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(block, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  RVE_CUDA_TRY(cudaLaunchKernelEx(&cfg, fn, arg));
+  return RVE_OK;
+}
+
 template <typename T, int NT, int NPT>
 int launch_node(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
   auto fn = dr_node_kernel<T, NT, NPT>;
@@ -37,9 +63,7 @@ int launch_node(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
   b.work = bin.d_work;
   b.n_work = bin.n;
   if (bin.check_every > 0) b.check_every = bin.check_every;
-  fn<<<bin.n, NT, bin.smem_node, s>>>(b);
-  RVE_CUDA_TRY(cudaGetLastError());
-  return RVE_OK;
+  return launch_k(fn, unsigned(bin.n), NT, bin.smem_node, s, bin.pdl, b);
 }
 
 template <typename T, int NT, int NPT, int MODE, int VAR>
@@ -66,9 +90,7 @@ int launch_variant(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
   b.work = bin.d_work;
   b.n_work = bin.n;
   if (bin.check_every > 0) b.check_every = bin.check_every;
-  fn<<<bin.n, NT, bin.smem, s>>>(b);
-  RVE_CUDA_TRY(cudaGetLastError());
-  return RVE_OK;
+  return launch_k(fn, unsigned(bin.n), NT, bin.smem, s, bin.pdl, b);
 }
 
 // One cluster of bin.cl CTAs per work item (streamed-size RVEs held in the

@@ -252,6 +252,10 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_node_kernel(const DrA
   __shared__ T sAB[2];
   __shared__ double sC;
 
+  // a launch that follows this one as a programmatic dependent (the rest of a
+  // bin whose costliest RVEs run here, one per SM) may start once every CTA
+  // of this launch is resident; it reads nothing written here
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const Work wk = A.work[blockIdx.x];
   const RveMeta M = A.meta[wk.rve];
   const int tid = threadIdx.x;
@@ -547,6 +551,7 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_node_kernel(const DrA
       if (A.iters) A.iters[wk.out] = it;
       if (A.status) A.status[wk.out] = status;
     }
+    pdl_epilogue(A);
     return;
   }
 
@@ -594,6 +599,7 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_node_kernel(const DrA
     if (A.iters) A.iters[wk.out] = it;
     if (A.status) A.status[wk.out] = st;
   }
+  pdl_epilogue(A);
 }
 
 }  // namespace rvegpu

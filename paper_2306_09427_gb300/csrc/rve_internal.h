@@ -205,6 +205,10 @@ struct DrArgs {
   ResumeRec* resume;       // per RVE
   T* vel;                  // 4 T per state node (velocity of a parked solve)
   double* energy;          // non-null: energy-balance variant, 6 doubles per output index
+  // non-null: this launch is a programmatic dependent of the launch before
+  // it on its stream (the rest of a bin whose costliest RVEs run there); its
+  // last CTA waits for that launch before it exits (counter, reset by it)
+  int32_t* pdl_done;
 };
 
 }  // namespace rvegpu

@@ -92,3 +92,27 @@ def test_kernel_timing_records_every_launch(rve):
     b.solve(Fd, stream=stream)
     assert b.last_kernel_ms().shape == (0,)
     b.close()
+
+
+def test_costliest_rves_on_their_own_sms_keep_results(rve):
+    """A whole-batch solve of a large resident bin launches the head of its
+    longest-first list on SMs of its own (high-priority stream); a subset
+    solve of the same RVEs runs one launch.  Same kernel and arithmetic, so
+    the stresses and iteration counts are identical, with and without a
+    captured graph."""
+    import torch
+    nets, Fs = rvegen.config_uniform(512, side=8)
+    Fd = _F(Fs)
+    for graphs in (0, 1):
+        b = rve.RveBatch(rvegen.pack(nets), precision=rve.RVE_PREC_MIXED, graphs=graphs)
+        assert len(b.bins()) in (0, 1)
+        stream = torch.cuda.Stream()
+        s_all, i_all, st = b.solve(Fd, stream=stream)   # learns the per-RVE cost
+        s_all, i_all, st = b.solve(Fd, stream=stream)   # longest first, costliest on their own SMs
+        torch.cuda.synchronize()
+        assert (st.cpu().numpy() == rve.RVE_STATUS_CONVERGED).all()
+        ids = np.arange(512)
+        s_sub, i_sub, _ = b.solve_subset(ids, Fd, stream=stream)
+        torch.cuda.synchronize()
+        assert torch.equal(s_all, s_sub) and torch.equal(i_all, i_sub)
+        b.close()
