@@ -93,14 +93,16 @@ def main():
     ap.add_argument("--max-wave", type=int, default=2048)
     ap.add_argument("--precision", type=int, default=RVE_PREC_MIXED, help="0 plain FP64 per RVE, 1 mixed, 2 FP64")
     ap.add_argument("--wave-iters", type=int, default=WAVE_ITERS, help="DR iterations per wave (0: whole solves)")
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="0 two-phase kernel, 2 node-centric kernels (clusters for RVEs too large for one CTA)")
     a = ap.parse_args()
     nets = pool_networks(a.pool)
-    b = RveBatch(rvegen.pack(nets), precision=a.precision, warm_start=1)
+    b = RveBatch(rvegen.pack(nets), precision=a.precision, warm_start=1, kernel=a.kernel)
     t, rve, F = request_stream(a.pool, a.rate, a.duration)
     wave = a.wave_iters if a.precision != 0 else 0
     res = run_poisson(b, t, rve, F, n_slots=a.slots, max_wave=a.max_wave, wave_iters=wave)
     out = {k: v for k, v in res.items() if not isinstance(v, np.ndarray)}
-    out.update(pool=a.pool, slots=a.slots, max_wave=a.max_wave, precision=a.precision)
+    out.update(pool=a.pool, slots=a.slots, max_wave=a.max_wave, precision=a.precision, kernel=a.kernel)
     print(json.dumps(out))
     b.close()
 
