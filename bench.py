@@ -57,10 +57,11 @@ BYTES_PER_FIBER_UPDATE = 20.0
 BYTES_PER_NODE_UPDATE = 52.0
 FP32_LANES_PER_SM = 128
 SMEM_BYTES_PER_CLK_PER_SM = 128
-# dram__bytes_read.sum + dram__bytes_write.sum of one fused-kernel launch on
-# this workload (ncu capture summarised in profiles/); None whenever the
-# kernel changes after that capture
-TRAFFIC_BYTES_PER_LAUNCH = 105.66e6 + 5.42e6
+# dram__bytes_read.sum + dram__bytes_write.sum of the fused kernel's 1016-RVE
+# launch on this workload (ncu capture summarised in profiles/; the 8-RVE
+# launch beside it adds about 1 %); None whenever the kernel changes after
+# that capture
+TRAFFIC_BYTES_PER_LAUNCH = 104.65e6 + 5.42e6
 
 
 def _config():
@@ -336,7 +337,7 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 9 * 8 * N_RVE,
                 "d2h_bytes_per_step": 9 * 8 * N_RVE + 2 * 4 * N_RVE},
         # per bin and step: the longest-first sort of the work list, then the fused solve
-        "gpu_launches": 2 * int(n_bins) * args.steps,
+        "gpu_launches": args.steps * sum(x["sorted"] + 1 + (x["exclusive"] > 0) for x in b.bins()),
         "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_LAUNCH, "traffic_unit": "bytes per launch",

@@ -350,12 +350,18 @@ int rve_batch_get_info(const rve_batch* b, rve_batch_info* info);
  *                 0 two-phase, 1 node-centric (one CTA per RVE),
  *                 2 node-centric over a cluster of `cluster` CTAs per RVE;
  *   cluster       CTAs per RVE of kernel 2 (0 otherwise);
- *   smem_bytes    dynamic shared memory per CTA of that kernel.
+ *   smem_bytes    dynamic shared memory per CTA of that kernel;
+ *   exclusive     RVEs of the bin that a whole-batch solve (rve_solve,
+ *                 rve_tangent) runs on SMs of their own, in a launch before
+ *                 the rest of the bin (the costliest by the longest-first
+ *                 order; 0: one launch);
+ *   sorted        1 when a longest-first sort kernel precedes the bin's
+ *                 launches.
  */
 typedef struct rve_bin_info {
   int32_t n_rve, mode, threads, nodes_per_thread, ctas_per_sm, check_every;
   int64_t smem_bytes;
-  int32_t kernel, cluster;
+  int32_t kernel, cluster, exclusive, sorted;
 } rve_bin_info;
 /* Fill up to max entries for `precision` (RVE_PREC_MIXED or _BATCHED_F64);
  * returns the number of bins (0 before the first batched solve). */

@@ -69,7 +69,7 @@ rve_set_positions = _sig("rve_set_positions", C.c_int, [_P, _I64, _P, _I32, _P])
 class rve_bin_info(C.Structure):
     _fields_ = [("n_rve", C.c_int32), ("mode", C.c_int32), ("threads", C.c_int32), ("nodes_per_thread", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("check_every", C.c_int32), ("smem_bytes", C.c_int64),
-                ("kernel", C.c_int32), ("cluster", C.c_int32)]
+                ("kernel", C.c_int32), ("cluster", C.c_int32), ("exclusive", C.c_int32), ("sorted", C.c_int32)]
 
 
 rve_batch_get_bins = _sig("rve_batch_get_bins", C.c_int, [_P, _I32, _I32, C.POINTER(rve_bin_info)])

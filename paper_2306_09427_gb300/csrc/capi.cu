@@ -1375,6 +1375,8 @@ int rve_batch_get_bins(const rve_batch* b, int32_t precision, int32_t max, rve_b
                        b->opt.damping_mode == RVE_DAMP_VISCOUS;
       out[n].kernel = 0;
       out[n].cluster = 0;
+      out[n].exclusive = P.bins.size() == 1 ? excl_count(x) : 0;
+      out[n].sorted = (x.d_sorted && x.n > 1 && x.n <= LPT_MAX) ? 1 : 0;
       out[n].smem_bytes = int64_t(x.smem);
       if (alt && x.mode == 0 && x.smem_node > 0) {
         out[n].kernel = 1;
