@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(NT, 1) dr_cluster_kernel(const DrArgs<T> A) {
     const double ez = sE[6] * q.dx + sE[7] * q.dy + sE[8] * q.dz;
     const double L02 = q.L0 * q.L0;
     const double a = (q.dx * ex + q.dy * ey + q.dz * ez + 0.5 * (q.dx * q.dx + q.dy * q.dy + q.dz * q.dz - L02)) / L02;
-    const double Na = law_f64(a, q.EA, q.B);
-    raff2 += Na * Na;
+    const T Na = law_t<T>(a, q.EA, q.B);
+    raff2 += double(Na * Na);
   }
   raff2 += boundary_stress_partials(A.fb + M.fb_off, nb, tid, NT, sF, sE, red);
   uint16_t* rank_of = reinterpret_cast<uint16_t*>(H1);  // holds nothing before the first update

@@ -153,7 +153,7 @@ __device__ __noinline__ void node_stress_partials(const V4* PP, const V4* H, con
   const int tid = threadIdx.x;
   if (g < 0) g = tid;  // the thread's index over the threads that share the RVE
   CSum s6[6];
-  double ps[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  T ps[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};  // check partials in the loop type (see add_virial)
 #pragma unroll
   for (int q = 0; q < NPT; ++q) {
     if (os.own[q] < 0) continue;
@@ -177,12 +177,12 @@ __device__ __noinline__ void node_stress_partials(const V4* PP, const V4* H, con
         s6[5].add(sd * dx * dy);
       } else {
         const T ox = sv * Dx, oy = sv * Dy, oz = sv * Dz;
-        ps[0] += double(ox * Dx);
-        ps[1] += double(oy * Dy);
-        ps[2] += double(oz * Dz);
-        ps[3] += double(oy * Dz);
-        ps[4] += double(ox * Dz);
-        ps[5] += double(ox * Dy);
+        ps[0] += ox * Dx;
+        ps[1] += oy * Dy;
+        ps[2] += oz * Dz;
+        ps[3] += oy * Dz;
+        ps[4] += ox * Dz;
+        ps[5] += ox * Dy;
       }
     }
   }
@@ -197,7 +197,7 @@ __device__ __noinline__ void node_stress_partials(const V4* PP, const V4* H, con
         red[(warp * 6 + k) * 2 + 1] = cc;
       }
     } else {
-      const double v = warp_sum(ps[k]);
+      const double v = warp_sum(double(ps[k]));
       if (lane == 0) red[warp * 9 + 3 + k] = v;
     }
   }
@@ -293,8 +293,8 @@ __global__ void __launch_bounds__(NT, min_blocks<NT>()) dr_node_kernel(const DrA
     const double ez = sE[6] * q.dx + sE[7] * q.dy + sE[8] * q.dz;
     const double L02 = q.L0 * q.L0;
     const double a = (q.dx * ex + q.dy * ey + q.dz * ez + 0.5 * (q.dx * q.dx + q.dy * q.dy + q.dz * q.dz - L02)) / L02;
-    const double Na = law_f64(a, q.EA, q.B);
-    raff2 += Na * Na;
+    const T Na = law_t<T>(a, q.EA, q.B);
+    raff2 += double(Na * Na);
   }
   raff2 += boundary_stress_partials(A.fb + M.fb_off, nb, tid, NT, sF, sE, red);
   // H positions are ranks in the decreasing-degree order (the owners of
