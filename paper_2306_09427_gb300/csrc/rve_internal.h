@@ -88,7 +88,10 @@ constexpr int VAR_ENERGY = 2;
 //                 to 1e-10 stopped on a weakly unstable equilibrium that the
 //                 oracle could not certify stable; the default DAMP_SCALE is
 //                 1.0 and the option damping_scale sets another.
-constexpr double MASS_GAMMA = 1.1;
+#ifndef RVE_MASS_GAMMA
+#define RVE_MASS_GAMMA 1.1
+#endif
+constexpr double MASS_GAMMA = RVE_MASS_GAMMA;
 constexpr double MASS_COEF = MASS_GAMMA * 0.25 * 2.0;
 constexpr double STEP_CAP = 0.1;
 constexpr double DAMP_C0 = 0.1;
