@@ -416,7 +416,10 @@ constexpr size_t KERNEL_TIMING_MAX = 65536;  // launches recorded per rve_set_ke
 // programmatic dependent launch, which starts as soon as every CTA of the
 // first has begun (so those are resident first) and runs beside it on the
 // other SMs.  Same kernel and arithmetic, so the results do not change.
-constexpr int EXCL_MAX = 8;                // RVEs given SMs of their own, per bin
+#ifndef RVE_EXCL_MAX
+#define RVE_EXCL_MAX 8
+#endif
+constexpr int EXCL_MAX = RVE_EXCL_MAX;     // RVEs given SMs of their own, per bin
 constexpr size_t EXCL_SMEM = 224 * 1024;   // dynamic shared memory of their CTAs
 int excl_count(const Bin& use) {
   if (use.mode != 0 || use.per_sm < 2 || use.n < 64) return 0;
