@@ -18,8 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.environ.get("RVE_LIB") or os.path.join(PKG, "librve.so")
 EXTRA = os.environ.get("RVE_NVCC_FLAGS", "").split()  # e.g. -DRVE_FIBER_UNROLL=1 for tuning builds
-SOURCES = ["dr_f32.cu", "dr_f64.cu", "dr_f32_kin.cu", "dr_f64_kin.cu", "dr_f32_ene.cu", "dr_f64_ene.cu", "dr_plain.cu",
-           "capi.cu", "serve.cu", "topology.cpp"]
+SOURCES = ["dr_f32.cu", "dr_f64.cu", "dr_f32_kin.cu", "dr_f64_kin.cu", "dr_f32_ene.cu", "dr_f64_ene.cu", "dr_node_launch.cu",
+           "dr_plain.cu", "capi.cu", "serve.cu", "topology.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

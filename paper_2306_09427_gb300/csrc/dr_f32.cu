@@ -5,10 +5,4 @@ namespace rvegpu {
 int launch_bin_viscous(const DrArgs<float>& a, const Bin& bin, cudaStream_t s) {
   return launch_bin_t<float, VAR_VISCOUS>(a, bin, s);
 }
-int cluster_capacity_f32(int npt, int cl, size_t smem, int* n_clusters) {
-  if (npt == 1) return cluster_capacity<float, 1>(cl, smem, n_clusters);
-  if (npt == 2) return cluster_capacity<float, 2>(cl, smem, n_clusters);
-  *n_clusters = 0;
-  return RVE_OK;
-}
 }  // namespace rvegpu

@@ -5,8 +5,6 @@
 
 #include "batch.h"
 #include "dr_fused.cuh"
-#include "dr_cluster.cuh"
-#include "dr_node.cuh"
 
 namespace rvegpu {
 
@@ -52,24 +50,16 @@ int launch_k(K fn, unsigned grid, unsigned block, size_t smem, cudaStream_t s, b
   return RVE_OK;
 }
 
-template <typename T, int NT, int NPT>
-int launch_node(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
-  auto fn = dr_node_kernel<T, NT, NPT>;
-  static int smem_set[64] = {};
-  static std::mutex smem_mu;
-  const int rc = set_smem(fn, bin.smem_node, smem_set, smem_mu);
-  if (rc != RVE_OK) return rc;
-  DrArgs<T> b = a;
-  b.work = bin.d_work;
-  b.n_work = bin.n;
-  if (bin.check_every > 0) b.check_every = bin.check_every;
-  return launch_k(fn, unsigned(bin.n), NT, bin.smem_node, s, bin.pdl, b);
-}
+// The node-centric and cluster kernels are instantiated in translation
+// units of their own (dr_node_launch.cu), compiled in parallel with these.
+int launch_node_any(const DrArgs<float>& a, const Bin& bin, cudaStream_t s);
+int launch_node_any(const DrArgs<double>& a, const Bin& bin, cudaStream_t s);
+int launch_cluster_any(const DrArgs<float>& a, const Bin& bin, cudaStream_t s);
 
 template <typename T, int NT, int NPT, int MODE, int VAR>
 int launch_variant(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
   if constexpr (MODE == 0 && VAR == VAR_VISCOUS) {
-    if (a.node_kernel && bin.smem_node > 0) return launch_node<T, NT, NPT>(a, bin, s);
+    if (a.node_kernel && bin.smem_node > 0) return launch_node_any(a, bin, s);
   }
   auto fn = dr_fused_kernel<T, NT, NPT, MODE, VAR>;
   // largest dynamic shared memory opted in so far, per device ordinal; the
@@ -93,72 +83,10 @@ int launch_variant(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
   return launch_k(fn, unsigned(bin.n), NT, bin.smem, s, bin.pdl, b);
 }
 
-// One cluster of bin.cl CTAs per work item (streamed-size RVEs held in the
-// cluster's distributed shared memory).
-// Opt the cluster kernel in to at least `smem` bytes of dynamic shared
-// memory; one cache per instantiation for the launches and the capacity
-// queries alike, so the attribute is only ever raised.
-template <typename T, int NPT>
-int cluster_smem(size_t smem) {
-  static int smem_set[64] = {};
-  static std::mutex smem_mu;
-  return set_smem(dr_cluster_kernel<T, CLUSTER_NT, NPT>, smem, smem_set, smem_mu);
-}
-
-template <typename T, int NPT>
-int launch_cluster(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
-  auto fn = dr_cluster_kernel<T, CLUSTER_NT, NPT>;
-  const int rc = cluster_smem<T, NPT>(bin.smem_cluster);
-  if (rc != RVE_OK) return rc;
-  DrArgs<T> b = a;
-  b.work = bin.d_work;
-  b.n_work = bin.n;
-  if (bin.check_every > 0) b.check_every = bin.check_every;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(bin.n) * unsigned(bin.cl), 1, 1);
-  cfg.blockDim = dim3(CLUSTER_NT, 1, 1);
-  cfg.dynamicSmemBytes = bin.smem_cluster;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = unsigned(bin.cl);
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  RVE_CUDA_TRY(cudaLaunchKernelEx(&cfg, fn, b));
-  return RVE_OK;
-}
-
-// Clusters of `cl` CTAs of the cluster kernel with `smem` bytes each that
-// the device can hold at once (0: the configuration cannot run).
-template <typename T, int NPT>
-int cluster_capacity(int cl, size_t smem, int* n_clusters) {
-  auto fn = dr_cluster_kernel<T, CLUSTER_NT, NPT>;
-  const int rc = cluster_smem<T, NPT>(smem);
-  if (rc != RVE_OK) return rc;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(cl), 1, 1);
-  cfg.blockDim = dim3(CLUSTER_NT, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = unsigned(cl);
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  RVE_CUDA_TRY(cudaOccupancyMaxActiveClusters(n_clusters, fn, &cfg));
-  return RVE_OK;
-}
-
 template <typename T, int NT, int NPT, int VAR>
 int launch_mode(const DrArgs<T>& a, const Bin& bin, cudaStream_t s) {
   if constexpr (VAR == VAR_VISCOUS && std::is_same<T, float>::value) {
-    if (bin.mode != 0 && bin.cl > 0 && a.node_kernel) {
-      if (bin.cl_npt == 1) return launch_cluster<T, 1>(a, bin, s);
-      if (bin.cl_npt == 2) return launch_cluster<T, 2>(a, bin, s);
-    }
+    if (bin.mode != 0 && bin.cl > 0 && a.node_kernel) return launch_cluster_any(a, bin, s);
   }
   switch (bin.mode) {
     case 0: return launch_variant<T, NT, NPT, 0, VAR>(a, bin, s);
