@@ -59,6 +59,7 @@ def build(lib, nets_):
     ncsr = np.zeros(max(nnodes, 1), np.uint32)
     ncap = np.zeros(max(nnodes, 1), np.float32)
     fid = np.zeros(max(nfree, 1), np.int32)
+    nord = np.zeros(max(nnodes, 1), np.uint16)
     lib.shim_meta(_ptr(meta))
     lib.shim_fa(_ptr(fa))
     lib.shim_fij(_ptr(fij))
@@ -66,7 +67,8 @@ def build(lib, nets_):
     lib.shim_ncsr(_ptr(ncsr))
     lib.shim_ncap(_ptr(ncap))
     lib.shim_free_ids(_ptr(fid))
-    return 0, dict(meta=meta, fa=fa, fij=fij, csr=csr, ncsr=ncsr, ncap=ncap, fid=fid, pruned=pruned)
+    lib.shim_nord(_ptr(nord))
+    return 0, dict(meta=meta, fa=fa, fij=fij, csr=csr, ncsr=ncsr, ncap=ncap, fid=fid, nord=nord, pruned=pruned)
 
 
 def wavefronts(idx):
@@ -185,3 +187,53 @@ def test_invalid_input_is_rejected(shim):
                          B=np.concatenate([net.B, [1.0]]), is_boundary=net.is_boundary, V0=1.0)
     rc, msg = build(shim, [bad])
     assert rc == -1 and "out of range" in msg
+
+
+def node_rank(q, t, nt):
+    """Position of thread t's q-th node in the decreasing-degree order (the
+    snake dealing of the node-centric kernels)."""
+    return (q + 1) * nt - 1 - t if q & 1 else q * nt + t
+
+
+def test_degree_order_and_node_dealing(shim):
+    """The node-centric kernels deal free nodes to threads in decreasing-degree
+    order: the order is a permutation of the free nodes sorted by decreasing
+    degree (ties by index), the snake dealing gives every node exactly one
+    (thread, slot), and it balances each thread's total degree."""
+    nets_, _ = rvegen.config_uniform(3)
+    nets_ += list(rvegen.config_uneven(3, side_hi=11)[0])
+    rc, T = build(shim, nets_)
+    assert rc == 0
+    for r in range(len(nets_)):
+        nf, na, _, node_off, _, _, csr_off, _ = (int(x) for x in T["meta"][r])
+        csr = T["csr"][csr_off:]
+        deg = np.zeros(nf, int)
+        for a in range(nf):
+            w = int(T["ncsr"][node_off + a])
+            run = csr[w >> 8:(w >> 8) + (w & 0xff)].astype(int)
+            deg[a] = int(((run >> 1) < na).sum())
+        order = T["nord"][node_off:node_off + nf].astype(int)
+        assert sorted(order.tolist()) == list(range(nf))
+        assert (np.diff(deg[order]) <= 0).all()
+        for k in range(nf - 1):  # ties by index
+            if deg[order[k]] == deg[order[k + 1]]:
+                assert order[k] < order[k + 1]
+        for nt in (64, 128, 256):
+            npt = max(1, -(-nf // nt))
+            npt = 1 if npt <= 1 else (2 if npt <= 2 else 4)
+            if nf > nt * npt:
+                continue
+            seen = set()
+            load = np.zeros(nt, int)
+            for t in range(nt):
+                for q in range(npt):
+                    k = node_rank(q, t, nt)
+                    if k < nf:
+                        assert k not in seen
+                        seen.add(k)
+                        load[t] += deg[order[k]]
+            assert seen == set(range(nf))
+            if npt == 2 and nf == 2 * nt:
+                # pairs of a high and a low degree: the spread of the loads is at
+                # most the spread of the degrees
+                assert load.max() - load.min() <= deg.max() - deg.min()

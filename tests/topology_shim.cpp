@@ -51,6 +51,7 @@ void shim_fij(uint32_t* out) { std::memcpy(out, g_topo.fij.data(), g_topo.fij.si
 void shim_csr(uint16_t* out) { std::memcpy(out, g_topo.csr.data(), g_topo.csr.size() * sizeof(uint16_t)); }
 void shim_ncsr(uint32_t* out) { std::memcpy(out, g_topo.ncsr.data(), g_topo.ncsr.size() * sizeof(uint32_t)); }
 void shim_ncap(float* out) { std::memcpy(out, g_topo.ncap.data(), g_topo.ncap.size() * sizeof(float)); }
+void shim_nord(uint16_t* out) { std::memcpy(out, g_topo.nord.data(), g_topo.nord.size() * sizeof(uint16_t)); }
 void shim_free_ids(int32_t* out) {
   std::memcpy(out, g_topo.free_node_id.data(), g_topo.free_node_id.size() * sizeof(int32_t));
 }
