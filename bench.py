@@ -61,7 +61,7 @@ SMEM_BYTES_PER_CLK_PER_SM = 128
 # launch on this workload (ncu capture summarised in profiles/; the 8-RVE
 # launch beside it adds about 1 %); None whenever the kernel changes after
 # that capture
-TRAFFIC_BYTES_PER_LAUNCH = 105.21e6 + 5.13e6
+TRAFFIC_BYTES_PER_LAUNCH = 104.73e6 + 5.09e6
 
 
 def _config():

@@ -281,27 +281,22 @@ __device__ __noinline__ void check_decide(const double* red, bool sig_test, int 
                                           double sigma_tol, int park_after, const double* thr,
                                           double (*sig)[8], const double* bb, T* ab, double* c_sh, int* flag_out) {
   const int lane = threadIdx.x & 31;
+  // cross-warp sums, one value per lane (warps in order), then lane 0
+  // collects them
+  const int nv = sig_test ? 9 : 3;
+  double s = 0.0;
+  if (lane < nv) {
+#pragma unroll 4
+    for (int w = 0; w < NW; ++w) s += red[w * 9 + lane];
+  }
   double v3[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) v3[k] = 0.0;
-  if (lane < NW) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) v3[k] = red[lane * 9 + k];
-    if (sig_test) {
-#pragma unroll
-      for (int k = 3; k < 9; ++k) v3[k] = red[lane * 9 + k];
-    }
-  }
-#pragma unroll
-  for (int o = NW / 2; o > 0; o >>= 1) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) v3[k] += __shfl_xor_sync(0xffffffffu, v3[k], o);
-    if (sig_test) {
-#pragma unroll
-      for (int k = 3; k < 9; ++k) v3[k] += __shfl_xor_sync(0xffffffffu, v3[k], o);
-    }
-  }
+  for (int k = 0; k < 9; ++k) v3[k] = __shfl_sync(0xffffffffu, s, k);
   if (lane != 0) return;
+  // The residual test and the stress differences stay in FP64; the ratios
+  // derived from them (the stress-convergence estimate, the damping
+  // estimate) are taken in the loop type T.
+  using R = T;
   int flag = -1;  // keep iterating; otherwise the final status
   if (!(v3[0] < 1e300)) {  // NaN or Inf
     flag = RVE_STATUS_NONFINITE;
@@ -312,22 +307,24 @@ __device__ __noinline__ void check_decide(const double* red, bool sig_test, int 
       // the stress and residual SIG_WINDOW checks back (ring of records)
       const double* prev = sig[(n_checks + 1) % (SIG_WINDOW + 1)];
       double* next = sig[n_checks % (SIG_WINDOW + 1)];
-      const double r = sqrt(v3[0]);
+      const R r = sqrt(R(v3[0]));
       double dn = 0.0, nn = 0.0;
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
         const double sg = v3[3 + k] + bb[2 * k] + bb[2 * k + 1];
+        const double d = sg - prev[k];
         const double wk2 = k < 3 ? 1.0 : 2.0;  // off-diagonal entries appear twice
-        dn += wk2 * (sg - prev[k]) * (sg - prev[k]);
+        dn += wk2 * d * d;
         nn += wk2 * sg * sg;
         next[k] = sg;
       }
       sig_ok = false;
-      if (prev[7] != 0.0 && nn > 0.0) {
-        const double rho = fmin(r / prev[6], SIG_RHO_CAP);
-        sig_ok = sqrt(dn / nn) * rho / (1.0 - rho) <= sigma_tol;
+      const R dnr = R(dn), nnr = R(nn);
+      if (prev[7] != 0.0 && nnr > R(0)) {
+        const R rho = fmin(r / R(prev[6]), R(SIG_RHO_CAP));
+        sig_ok = sqrt(dnr / nnr) * rho / (R(1) - rho) <= R(sigma_tol);
       }
-      next[6] = r;
+      next[6] = double(r);
       next[7] = 1.0;
     } else if (sig_test) {
       sig[n_checks % (SIG_WINDOW + 1)][7] = 0.0;
@@ -338,12 +335,12 @@ __device__ __noinline__ void check_decide(const double* red, bool sig_test, int 
       flag = RVE_STATUS_MAX_ITER;
     } else {
       if (adaptive && have_pre && v3[2] > 0.0) {
-        const double lam = -v3[1] / v3[2];
-        if (lam > 0.0) {
-          const double c = fmin(damping_scale * 2.0 * sqrt(lam), DAMP_C_MAX);
-          *c_sh = c;
-          ab[0] = T((2.0 - c) / (2.0 + c));
-          ab[1] = T(2.0 / (2.0 + c));
+        const R lam = -R(v3[1]) / R(v3[2]);
+        if (lam > R(0)) {
+          const R c = fmin(R(damping_scale) * R(2) * sqrt(lam), R(DAMP_C_MAX));
+          *c_sh = double(c);
+          ab[0] = T((R(2) - c) / (R(2) + c));
+          ab[1] = T(R(2) / (R(2) + c));
         }
       }
       // end of a serving wave: park before the update of this iteration
