@@ -21,7 +21,8 @@
 //            per-thread, per-warp and cross-warp sums in FP64)
 //            against max(tol R_aff, 1e-16 sum EA) and, with sigma_tol > 0,
 //            the estimated remaining stress error; damping re-estimated,
-//            c = s 2 sqrt(lambda) from the Rayleigh quotient lambda; thread 0
+//            c = s 2 sqrt(lambda) from the Rayleigh quotient lambda (the
+//            stress-error estimate and c in T, from the FP64 sums); thread 0
 //            takes these block-uniform decisions and publishes them;
 //     update m = MASS_COEF sbar_sum, v <- ((2-c) v + 2 f/m)/(2+c),
 //            |v| capped, h <- h + v (dt = 1); with VAR_KINETIC (kinetic damping)
